@@ -1,0 +1,332 @@
+"""RGF transmission throughput benchmark (energy points per second).
+
+Workload: the doped metal-semiconductor-metal junction with 500 principal
+layers of block size 256 (2048 energies in [-1.5, 1.5] eV, eta = 1e-6,
+synthetic seeded Hamiltonian).  One step = one wave of energies through the
+whole path: decimation of both leads, self-energies, the 500-layer sweep and
+the Caroli trace.  Ranks (torchrun) take disjoint energy waves; there is no
+data-path collective.
+
+Prints one JSON line.  See --help for the options.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "doped_N500_b256"
+METRIC = "RGF energy-points/s (b=256, 500 layers), mixed vs FP64 at |dT|<=1e-6; p99 ms"
+# ncu DRAM traffic of one slice-product GEMM launch (dram__bytes_read.sum +
+# dram__bytes_write.sum) and the source it was measured on; reported only
+# while that source is unchanged.
+GEMM_TRAFFIC = None  # (bytes_per_launch, batch, sha256 of tc_gemm.cu)
+
+
+def parse():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--wave", type=int, default=148, help="energies per step and rank")
+    ap.add_argument("--fp64-wave", type=int, default=16, help="energies of the FP64 GPU comparison step")
+    ap.add_argument("--no-compare", action="store_true", help="skip the FP64 GPU comparison step")
+    ap.add_argument("--cpu-energies", type=int, default=2, help="energies of the oracle CPU sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 7:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for s in self.samples:
+            try:
+                sm.append(float(s[0]))
+                mx = float(s[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, s[3:]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d, "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}, "fallback"
+
+
+def oracle_sample(dev, E, eta, n):
+    """FP64 oracle on the first n energies; returns (T, seconds, threads)."""
+    from oracle import rgf_oracle as o
+    try:
+        from threadpoolctl import threadpool_info
+        threads = max((i.get("num_threads", 1) for i in threadpool_info()), default=1)
+    except Exception:
+        threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    T = o.transmission(dev, E[:n], eta)
+    return T, time.perf_counter() - t0, threads
+
+
+def tc_source_hash():
+    import hashlib
+    with open(os.path.join(ROOT, "paper_2609_37058_b300", "csrc", "tc_gemm.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()
+
+
+def run_reference(args, rank, world):
+    """The oracle, as it stands, on the host cores: each step is a bounded
+    sample (one energy) of the same workload."""
+    if rank != 0:
+        return
+    from synth import make_workload
+    dev, E, eta = make_workload(WORKLOAD)
+    times, threads = [], 1
+    for k in range(args.warmup + args.steps):
+        _, dt, threads = oracle_sample(dev, E[k % len(E):], eta, 1)
+        if k >= args.warmup:
+            times.append(dt)
+    per = sum(times) / len(times)
+    value = 1.0 / per
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "energy-points/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded junction Hamiltonian)",
+        "config": {"workload": WORKLOAD, "n_layers": 500, "b": 256, "energies_per_step": 1, "eta": 1e-6},
+        "cpu_baseline": {"value": value, "unit": "energy-points/s", "cores": threads, "kind": "oracle",
+                         "sample": f"1 energy per step of {WORKLOAD}, numpy FP64 oracle"},
+        "e2e": {"value": value, "unit": "energy-points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import numpy as np
+    import torch
+
+    from paper_2609_37058_b300 import rgf
+    from synth import make_workload
+
+    torch.cuda.set_device(local)
+    dev, E_all, eta = make_workload(WORKLOAD)
+    n_E = len(E_all)
+    W = args.wave
+    prec = rgf.RGF_MIXED if args.precision == "mixed" else rgf.RGF_FP64
+    stream = torch.cuda.Stream()
+    plan = rgf.Plan(dev.n_layers, dev.b, precision=prec, eta=eta, energy_wave=W, cuda_stream=stream.cuda_stream)
+    plan.set_device(dev)
+    E_d = torch.tensor(E_all, dtype=torch.float64, device="cuda")
+    T_d = torch.zeros(n_E, dtype=torch.float64, device="cuda")
+
+    def wave(k):
+        start = ((k * world + rank) * W) % n_E
+        return start, min(W, n_E - start)
+
+    def step(k):
+        s, c = wave(k)
+        rgf.rgf_transmission(plan.handle, E_d[s:s + c], T_d[s:s + c])
+        return c
+
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    clocks = ClockSampler(local)
+    rgf.rgf_gemm_timing(True)
+    launches0 = rgf.rgf_launch_count()
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    step_ms = []
+    ev0.record(stream)
+    done = 0
+    for k in range(args.warmup, args.warmup + args.steps):
+        a = torch.cuda.Event(enable_timing=True)
+        b_ = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        done += step(k)
+        b_.record(stream)
+        step_ms.append((a, b_))
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks.stop()
+    launches = rgf.rgf_launch_count() - launches0
+    gemm_ms, gemm_n, gemm_flops = rgf.rgf_gemm_timing(False)
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    per_step = [a.elapsed_time(b_) for a, b_ in step_ms]
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([elapsed], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+        n = torch.tensor([done], device="cuda", dtype=torch.float64)
+        dist.all_reduce(n)
+        done_all = float(n.item())
+    else:
+        done_all = float(done)
+    value = done_all / elapsed
+    T_timed = T_d.cpu().numpy()
+
+    if rank != 0:
+        plan.close()
+        return
+
+    # ---------------------------------------------------------- end to end
+    # The public call a user makes, from host buffers: upload the blocks and
+    # leads, then T(E) for one wave of host energies into host arrays.
+    s, c = wave(args.warmup)
+    E_h = np.ascontiguousarray(E_all[s:s + c])
+    T_h = np.empty_like(E_h)
+    err_h = np.empty_like(E_h)
+    fl_h = np.empty(c, dtype=np.int32)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plan.set_device(dev)
+    rgf.rgf_transmission(plan.handle, E_h, T_h, err_h, fl_h)
+    e2e_s = time.perf_counter() - t0
+    h2d = dev.nbytes() + sum(getattr(l, f).nbytes for l in (dev.lead_L, dev.lead_R)
+                             for f in ("H00", "S00", "H10", "S10", "Hc", "Sc")) + E_h.nbytes
+    d2h = T_h.nbytes + err_h.nbytes + fl_h.nbytes
+    waves_done, reseeds = plan.stats
+    plan.close()
+
+    # ---------------------------------------------------------- FP64 GPU path
+    fp64 = None
+    if not args.no_compare and prec == rgf.RGF_MIXED:
+        Wf = args.fp64_wave
+        with rgf.Plan(dev.n_layers, dev.b, precision=rgf.RGF_FP64, eta=eta, energy_wave=Wf,
+                      cuda_stream=stream.cuda_stream) as pf:
+            pf.set_device(dev)
+            Ef = np.ascontiguousarray(E_all[:Wf])
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            Tf, _, _ = pf.transmission(Ef)
+            dtf = time.perf_counter() - t0
+        fp64 = {"value": Wf / dtf, "unit": "energy-points/s", "energies": Wf,
+                "max_abs_dT_vs_mixed": float(np.abs(Tf - T_timed[:Wf]).max()) if T_timed[:Wf].any() else None}
+
+    # ---------------------------------------------------------- CPU oracle
+    s0, _ = wave(args.warmup)
+    nb = args.cpu_energies
+    T_cpu, cpu_s, threads = oracle_sample(dev, E_all[s0:], eta, nb)
+    dT = np.abs(T_cpu - T_timed[s0:s0 + nb])
+
+    peaks, peak_src = measured_peaks()
+    peak = float(peaks.get("bf16_tflops_sustained", 1400.0))
+    roof = None
+    if gemm_ms > 0:
+        achieved = gemm_flops / (gemm_ms / 1e3) / 1e12
+        traffic = None
+        if GEMM_TRAFFIC is not None and GEMM_TRAFFIC[2] == tc_source_hash():
+            traffic = GEMM_TRAFFIC[0] * (gemm_flops / gemm_n) / GEMM_TRAFFIC[1] if gemm_n else None
+        roof = {"bound": "tensor", "kernel": "k_oz_tc (slice-product GEMM, tcgen05)", "achieved": achieved,
+                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+                "peak_source": f"bf16_tflops_sustained of {peak_src}", "launches": gemm_n,
+                "avg_launch_ms": gemm_ms / max(gemm_n, 1),
+                "work": "BF16 flops of 21 slice-pair products, 2*M*N*K each (M=b, N=2b, K=2b)"}
+    clk = clocks.summary()
+    steps_sorted = sorted(per_step)
+    p99 = steps_sorted[min(len(steps_sorted) - 1, int(round(0.99 * (len(steps_sorted) - 1))))]
+    line = {
+        "metric": METRIC, "value": value, "unit": "energy-points/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed * 1e3 / args.steps, "p50_ms": statistics.median(per_step),
+        "p99_ms": p99, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16-slices/df32" if prec == rgf.RGF_MIXED else "f64",
+        "data": "synthetic (seeded doped-junction Hamiltonian, Pt-Si:P-Pt-like)",
+        "config": {"workload": WORKLOAD, "n_layers": dev.n_layers, "b": dev.b, "energies_per_step": W,
+                   "eta": eta, "precision": args.precision, "parallelism": f"energy waves x{world}",
+                   "l2": "inputs larger than L2 (2.1 GB of blocks, GBs of wave workspace)"},
+        "gpu_launches": int(launches),
+        "e2e": {"value": c / e2e_s, "unit": "energy-points/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "roofline": roof,
+        "cpu_baseline": {"value": nb / cpu_s, "unit": "energy-points/s", "cores": threads, "kind": "oracle",
+                         "sample": f"first {nb} energies of the first timed wave, numpy FP64 oracle"},
+        "parity_sample": {"energies": nb, "max_abs_dT": float(dT.max()), "bar": 1e-6},
+        "fp64_gpu": fp64,
+        "fp64_reseeds": reseeds,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

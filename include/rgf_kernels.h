@@ -1,0 +1,57 @@
+/*
+ * rgf_kernels.h - kernel-level entry points of the RGF library, for tests
+ * and benchmarks of single building blocks (same conventions as rgf.h:
+ * complex matrices are row-major (re, im) double pairs, batch-major; all
+ * pointers are HOST memory; the calls are synchronous; a non-OK status
+ * leaves a message for rgf_last_error()).  They allocate their own
+ * temporary device memory for the duration of the call.
+ */
+#ifndef RGF_KERNELS_H
+#define RGF_KERNELS_H
+
+#include "rgf.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* C[i] = A[i] B[i], i < batch; A m x k, B k x n, C m x n, all FP64 (the
+ * FP64 path's CUDA-core GEMM). */
+rgf_status rgf_kernel_zgemm_f64(int batch, int m, int n, int k, const double* A, const double* B, double* C);
+
+/* In-place inverse of batch b x b matrices by the FP64 path's blocked
+ * Gauss-Jordan elimination with partial pivoting.  flags[i] (may be NULL)
+ * gets RGF_FLAG_SINGULAR for an exactly zero pivot. */
+rgf_status rgf_kernel_inverse_f64(int batch, int b, double* A, int* flags);
+
+/* In-place FP32 inverse (the mixed path's seed): A holds complex64 values
+ * as (re, im) float pairs. */
+rgf_status rgf_kernel_inverse_c64(int batch, int b, float* A, int* flags);
+
+/* C[i] = A[i] B[i] by the mixed path's slice-product GEMM: A and B are
+ * rounded to double-float, split into six BF16 slices each and multiplied
+ * on the tensor cores; C is the double-float result widened to FP64.
+ * core = 0: tcgen05 (TMA, TMEM accumulators); core = 1: the legacy
+ * warp-level mma.sync path. */
+rgf_status rgf_kernel_zgemm_mixed(int batch, int m, int n, int k, const double* A, const double* B, double* C,
+                                  int core);
+
+/* Counters for measurement (process-wide, thread-safe). */
+
+/* Number of CUDA kernel launches issued by the library since load. */
+unsigned long long rgf_launch_count(void);
+
+/* CUDA-event timing of the mixed path's slice-product GEMM (tcgen05 core),
+ * recorded on the stream each launch runs on.  A call returns the totals of
+ * the launches recorded since the previous call (total_ms: summed launch
+ * durations; launches; flops: BF16 tensor flops executed, 21 slice-pair
+ * products of 2 M N K each), clears them, and turns recording on
+ * (enable != 0) or off.  Outputs may be NULL.  Only launches without an
+ * energy mask are recorded. */
+rgf_status rgf_gemm_timing(int enable, double* total_ms, long long* launches, double* flops);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RGF_KERNELS_H */

@@ -1,0 +1,318 @@
+// Batched complex GEMM and blocked Gauss-Jordan inverse on the CUDA cores,
+// templated on the complex element type (double2 for the FP64 path, float2
+// for the FP32 seed inverse of the mixed path).
+#pragma once
+
+#include "kernels.h"
+
+namespace rgf {
+
+template <typename T2> struct CT;
+template <> struct CT<double2> {
+    using R = double;
+    static __host__ __device__ __forceinline__ double2 make(double a, double b) { return make_double2(a, b); }
+};
+template <> struct CT<float2> {
+    using R = float;
+    static __host__ __device__ __forceinline__ float2 make(float a, float b) { return make_float2(a, b); }
+};
+
+__host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+
+// 64 x 64 complex output tile per CTA, K step 16, 256 threads each owning a
+// 4 x 4 set of outputs strided by 16 so shared-memory reads are broadcasts
+// (A) or consecutive (B).
+constexpr int ZG_BM = 64, ZG_BN = 64, ZG_BK = 16;
+
+template <typename T2>
+__global__ void __launch_bounds__(256) k_zgemm(GemmArgs<T2> g) {
+    using C = CT<T2>;
+    const int bi = blockIdx.z;
+    if (g.active && !g.active[bi]) return;
+    const int m0 = blockIdx.y * ZG_BM, n0 = blockIdx.x * ZG_BN;
+    if (n0 >= g.skip0 && n0 + ZG_BN <= g.skip1) return;
+    const T2* __restrict__ A = g.A + (long)bi * g.sA;
+    const T2* __restrict__ B = g.B + (long)bi * g.sB;
+    __shared__ T2 As[ZG_BK][ZG_BM];
+    __shared__ T2 Bs[ZG_BK][ZG_BN];
+    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+    T2 acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = C::make(0, 0);
+
+    for (int k0 = 0; k0 < g.k; k0 += ZG_BK) {
+#pragma unroll
+        for (int t = 0; t < (ZG_BM * ZG_BK) / 256; ++t) {
+            const int i = tid + t * 256;
+            const int r = i / ZG_BK, kk = i % ZG_BK;
+            const int gr = m0 + r, gk = k0 + kk;
+            As[kk][r] = (gr < g.m && gk < g.k) ? A[(long)gr * g.lda + gk] : C::make(0, 0);
+        }
+#pragma unroll
+        for (int t = 0; t < (ZG_BK * ZG_BN) / 256; ++t) {
+            const int i = tid + t * 256;
+            const int kk = i / ZG_BN, c = i % ZG_BN;
+            const int gk = k0 + kk, gc = n0 + c;
+            Bs[kk][c] = (gk < g.k && gc < g.n) ? B[(long)gk * g.ldb + gc] : C::make(0, 0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < ZG_BK; ++kk) {
+            T2 a[4], bb[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) bb[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) cfma(acc[i][j], a[i], bb[j]);
+        }
+        __syncthreads();
+    }
+    const T2* Cin = g.Cin ? g.Cin + (long)bi * g.sCin : nullptr;
+    T2* Cp = g.C + (long)bi * g.sC;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int r = m0 + ty + 16 * i;
+        if (r >= g.m) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int c = n0 + tx + 16 * j;
+            if (c >= g.n || (c >= g.skip0 && c < g.skip1)) continue;
+            T2 v = cmul(g.alpha, acc[i][j]);
+            if (Cin) v = cadd(v, cmul(g.beta, Cin[(long)r * g.ldcin + c]));
+            Cp[(long)r * g.ldc + c] = v;
+        }
+    }
+}
+
+template <typename T2>
+rgf_status zgemm_t(const GemmArgs<T2>& g, cudaStream_t st) {
+    if (g.batch <= 0 || g.m <= 0 || g.n <= 0) return RGF_OK;
+    if (g.batch > 65535) {
+        set_error("zgemm: batch %d > 65535", g.batch);
+        return RGF_E_INVALID;
+    }
+    dim3 grid(ceil_div(g.n, ZG_BN), ceil_div(g.m, ZG_BM), g.batch);
+    k_zgemm<T2><<<grid, 256, 0, st>>>(g);
+    RGF_LAUNCH_CHECK();
+    return RGF_OK;
+}
+
+// ------------------------------------------------------------------ inverse
+// Blocked Gauss-Jordan with partial pivoting, in place.  For each panel of
+// nb columns K = [k0, k0+nb):
+//  1. panel kernel: unblocked in-place Gauss-Jordan on the b x nb panel
+//     (pivot search among the rows not yet used as pivots, row swaps inside
+//     the panel), giving [-A_0K A_KK^-1; A_KK^-1; -A_2K A_KK^-1]; it also
+//     writes Pbar = that panel minus the identity on the K x K block;
+//  2. swap kernel: applies the panel's row swaps to the other columns and
+//     copies rows K of those columns into T (nb x b);
+//  3. GEMM: A[:, not K] += Pbar T.
+// At the end the column interchanges are undone in reverse order.
+static inline int gj_nb(int b) { return b <= 320 ? (b < 32 ? b : 32) : 16; }
+
+template <typename T2>
+size_t inv_workspace_bytes_t(int batch, int b) {
+    const int nb = gj_nb(b);
+    return (size_t)batch * ((size_t)b * nb * sizeof(T2) * 2 + (size_t)b * sizeof(int)) + 256;
+}
+
+template <typename R>
+__device__ __forceinline__ void argmax_merge(R& v, int& i, R v2, int i2) {
+    if (v2 > v || (v2 == v && i2 < i)) {
+        v = v2;
+        i = i2;
+    }
+}
+
+template <typename T2>
+__global__ void __launch_bounds__(256) k_gj_panel(int b, int k0, int nbk, T2* A, long sA, T2* Pbar, int* piv,
+                                                  int* flags, const int* active) {
+    using C = CT<T2>;
+    using R = typename C::R;
+    const int bi = blockIdx.x;
+    if (active && !active[bi]) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T2* pan = reinterpret_cast<T2*>(smem_raw);  // b x nbk
+    T2* fcol = pan + (long)b * nbk;              // b
+    __shared__ R red_v[8];
+    __shared__ int red_i[8];
+    __shared__ int s_piv;
+    T2* Ab = A + (long)bi * sA;
+    int* pv = piv + (long)bi * b;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+
+    for (int i = tid; i < b * nbk; i += blockDim.x) {
+        const int r = i / nbk, c = i % nbk;
+        pan[i] = Ab[(long)r * b + k0 + c];
+    }
+    __syncthreads();
+
+    for (int jj = 0; jj < nbk; ++jj) {
+        const int j = k0 + jj;
+        R bv = -1;
+        int bidx = b;
+        for (int r = j + tid; r < b; r += blockDim.x) argmax_merge<R>(bv, bidx, cabs2(pan[r * nbk + jj]), r);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            R ov = __shfl_down_sync(0xffffffffu, bv, off);
+            int oi = __shfl_down_sync(0xffffffffu, bidx, off);
+            argmax_merge<R>(bv, bidx, ov, oi);
+        }
+        if (lane == 0) {
+            red_v[wid] = bv;
+            red_i[wid] = bidx;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            R v = red_v[0];
+            int ix = red_i[0];
+            for (int w = 1; w < (int)(blockDim.x >> 5); ++w) argmax_merge<R>(v, ix, red_v[w], red_i[w]);
+            if (ix >= b) ix = j;
+            s_piv = ix;
+            pv[j] = ix;
+            if (!(v > 0) && flags) atomicOr(&flags[bi], RGF_FLAG_SINGULAR);
+        }
+        __syncthreads();
+        const int p = s_piv;
+        if (p != j) {
+            for (int c = tid; c < nbk; c += blockDim.x) {
+                T2 t = pan[j * nbk + c];
+                pan[j * nbk + c] = pan[p * nbk + c];
+                pan[p * nbk + c] = t;
+            }
+        }
+        __syncthreads();
+        const T2 inv_d = cinv(pan[j * nbk + jj]);
+        for (int r = tid; r < b; r += blockDim.x) fcol[r] = pan[r * nbk + jj];
+        __syncthreads();
+        for (int c = tid; c < nbk; c += blockDim.x)
+            pan[j * nbk + c] = (c == jj) ? inv_d : cmul(pan[j * nbk + c], inv_d);
+        __syncthreads();
+        for (int i = tid; i < b * nbk; i += blockDim.x) {
+            const int r = i / nbk, c = i % nbk;
+            if (r == j) continue;
+            const T2 f = fcol[r];
+            if (c == jj) {
+                pan[i] = cmul(C::make(-f.x, -f.y), inv_d);
+            } else {
+                T2 v = pan[i];
+                const T2 pj = pan[j * nbk + c];
+                v.x -= f.x * pj.x - f.y * pj.y;
+                v.y -= f.x * pj.y + f.y * pj.x;
+                pan[i] = v;
+            }
+        }
+        __syncthreads();
+    }
+    T2* Pb = Pbar + (long)bi * b * nbk;
+    for (int i = tid; i < b * nbk; i += blockDim.x) {
+        const int r = i / nbk, c = i % nbk;
+        T2 v = pan[i];
+        Ab[(long)r * b + k0 + c] = v;
+        if (r == k0 + c) v.x -= 1;
+        Pb[i] = v;
+    }
+}
+
+template <typename T2>
+__global__ void k_gj_swap(int b, int k0, int nbk, T2* A, long sA, const int* piv, T2* T, const int* active) {
+    const int bi = blockIdx.y;
+    if (active && !active[bi]) return;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= b) return;
+    T2* Ab = A + (long)bi * sA;
+    T2* Tb = T + (long)bi * nbk * b;
+    const int* pv = piv + (long)bi * b;
+    if (c >= k0 && c < k0 + nbk) {
+        for (int jj = 0; jj < nbk; ++jj) Tb[(long)jj * b + c] = CT<T2>::make(0, 0);
+        return;
+    }
+    for (int jj = 0; jj < nbk; ++jj) {
+        const int j = k0 + jj, p = pv[j];
+        if (p != j) {
+            T2 t = Ab[(long)j * b + c];
+            Ab[(long)j * b + c] = Ab[(long)p * b + c];
+            Ab[(long)p * b + c] = t;
+        }
+    }
+    for (int jj = 0; jj < nbk; ++jj) Tb[(long)jj * b + c] = Ab[(long)(k0 + jj) * b + c];
+}
+
+template <typename T2>
+__global__ void k_gj_unpermute(int b, T2* A, long sA, const int* piv, const int* active) {
+    const int bi = blockIdx.y;
+    if (active && !active[bi]) return;
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= b) return;
+    T2* row = A + (long)bi * sA + (long)r * b;
+    const int* pv = piv + (long)bi * b;
+    for (int j = b - 1; j >= 0; --j) {
+        const int p = pv[j];
+        if (p != j) {
+            T2 t = row[j];
+            row[j] = row[p];
+            row[p] = t;
+        }
+    }
+}
+
+template <typename T2>
+rgf_status inv_t(int batch, int b, T2* A, long sA, void* ws, int* flags, const int* active, cudaStream_t st) {
+    if (batch <= 0) return RGF_OK;
+    const int nb = gj_nb(b);
+    T2* Pbar = (T2*)ws;
+    T2* T = Pbar + (size_t)batch * b * nb;
+    int* piv = (int*)(T + (size_t)batch * b * nb);
+    const size_t smem = ((size_t)b * nb + b) * sizeof(T2);
+    if (smem > 200 * 1024) {
+        set_error("inverse: b = %d needs %zu bytes of shared memory", b, smem);
+        return RGF_E_INVALID;
+    }
+    if (smem > 48 * 1024)
+        RGF_CUDA_TRY(cudaFuncSetAttribute(k_gj_panel<T2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    for (int k0 = 0; k0 < b; k0 += nb) {
+        const int nbk = (b - k0) < nb ? (b - k0) : nb;
+        const size_t sm = ((size_t)b * nbk + b) * sizeof(T2);
+        k_gj_panel<T2><<<batch, 256, sm, st>>>(b, k0, nbk, A, sA, Pbar, piv, flags, active);
+        RGF_LAUNCH_CHECK();
+        if (nbk < b) {
+            dim3 g2(ceil_div(b, 128), batch);
+            k_gj_swap<T2><<<g2, 128, 0, st>>>(b, k0, nbk, A, sA, piv, T, active);
+            RGF_LAUNCH_CHECK();
+            GemmArgs<T2> g{};
+            g.batch = batch;
+            g.m = b;
+            g.n = b;
+            g.k = nbk;
+            g.alpha = CT<T2>::make(1, 0);
+            g.beta = CT<T2>::make(1, 0);
+            g.A = Pbar;
+            g.lda = nbk;
+            g.sA = (long)b * nbk;
+            g.B = T;
+            g.ldb = b;
+            g.sB = (long)nbk * b;
+            g.Cin = A;
+            g.ldcin = b;
+            g.sCin = sA;
+            g.C = A;
+            g.ldc = b;
+            g.sC = sA;
+            g.active = active;
+            g.skip0 = k0;
+            g.skip1 = k0 + nbk;
+            RGF_TRY(zgemm_t<T2>(g, st));
+        }
+    }
+    dim3 g3(ceil_div(b, 128), batch);
+    k_gj_unpermute<T2><<<g3, 128, 0, st>>>(b, A, sA, piv, active);
+    RGF_LAUNCH_CHECK();
+    return RGF_OK;
+}
+
+}  // namespace rgf

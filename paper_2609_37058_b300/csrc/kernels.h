@@ -1,0 +1,78 @@
+// Kernel launch wrappers of the RGF library (host-callable, stream-ordered).
+#pragma once
+
+#include "common.cuh"
+
+namespace rgf {
+
+// Source blocks of a batched "z S - H" formation.  Batch entry be = s*W + e
+// (s = side/source index < nsrc, e = energy index < W) reads S[s], H[s]
+// (b x b, row-major complex128) and, when trans[s] != 0, their conjugate
+// transposes.  S[s] == nullptr means S = 0.
+struct FormSrc {
+    const double2* S[2];
+    const double2* H[2];
+    int trans[2];
+};
+
+// out[be] = (E[e] + i eta) S' - H' - sub_coef * sub[be]   (sub may be null)
+rgf_status form_f64(int W, int nsrc, int b, const double* E, double eta, const FormSrc& src,
+                    double2* out, const double2* sub, double sub_coef, const int* active,
+                    cudaStream_t st);
+
+// Batched complex GEMM in FP64:  C[i] = alpha * A[i] B[i] + beta * Cin[i]
+// for i < batch, A m x k (lda), B k x n (ldb), C m x n (ldc); batch strides
+// in elements (0 = shared operand).  Columns [skip0, skip1) of C are not
+// written.  active (may be null) masks batch entries.  Cin may alias C.
+template <typename T2>
+struct GemmArgs {
+    int batch, m, n, k;
+    T2 alpha, beta;
+    const T2* A; long lda, sA;
+    const T2* B; long ldb, sB;
+    const T2* Cin; long ldcin, sCin;
+    T2* C; long ldc, sC;
+    const int* active;
+    int skip0, skip1;
+};
+using ZGemm = GemmArgs<double2>;
+rgf_status zgemm_f64(const ZGemm& g, cudaStream_t st);
+
+// In-place batched inverse of b x b complex128 matrices by blocked
+// Gauss-Jordan elimination with partial (row) pivoting.  ws must hold
+// inv_f64_workspace_bytes(batch, b) bytes.  flags[i] |= RGF_FLAG_SINGULAR on
+// an exactly zero pivot (flags may be null).
+size_t inv_f64_workspace_bytes(int batch, int b);
+rgf_status inv_f64(int batch, int b, double2* A, long sA, void* ws, int* flags,
+                   const int* active, cudaStream_t st);
+
+// Elementwise helpers (batch of b x b matrices, stride b*b).
+rgf_status set_identity_f64(int batch, int b, double2* A, cudaStream_t st);
+// eps_s -= agb ; eps -= agb + bga   (decimation update)
+rgf_status dec_update_f64(int batch, int b, double2* eps_s, double2* eps, const double2* agb,
+                          const double2* bga, const int* active, cudaStream_t st);
+// gamma = i (sigma - sigma^dagger)
+rgf_status gamma_f64(int batch, int b, const double2* sigma, double2* gamma, cudaStream_t st);
+// Decimation convergence: for active i, if max(|alpha_i|_F, |beta_i|_F) <=
+// tol * anorm[i] then active[i] = 0; iters[i] = it while active; counts the
+// entries still active into *remaining (zeroed by the caller).
+rgf_status dec_check_f64(int batch, int b, const double2* alpha, const double2* beta,
+                         const double* anorm, double tol, int it, int* active, int* iters,
+                         int* remaining, cudaStream_t st);
+// anorm[i] = |A_i|_F
+rgf_status fro_norm_f64(int batch, int b, const double2* A, double* out, cudaStream_t st);
+// T[i] = Re sum_jk X_jk conj(Y_jk); Timag[i] = Im of the same sum.
+rgf_status trace_xy_f64(int batch, int b, const double2* X, const double2* Y, double* T,
+                        double* Timag, cudaStream_t st);
+// Copy with batch masks: dst[i] = src[i] for active i.
+rgf_status copy_f64(int batch, int b, double2* dst, const double2* src, const int* active,
+                    cudaStream_t st);
+
+// Y[i] += alpha * X[i]  (real alpha)
+rgf_status axpy_f64(int batch, int b, double alpha, const double2* X, double2* Y, cudaStream_t st);
+// flags[e] |= dec_flags[e] | dec_flags[W+e] | NOCONV bits from the
+// decimation active masks (still active after the last iteration).
+rgf_status merge_dec_flags(int W, const int* dec_flags, const int* dec_active, int* flags,
+                           cudaStream_t st);
+
+}  // namespace rgf

@@ -1,0 +1,108 @@
+// Mixed-precision building blocks: double-float complex matrices (float4
+// per element: re_hi, re_lo, im_hi, im_lo), their BF16 slice expansions and
+// the exact slice-product complex GEMM.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "kernels.h"
+
+namespace rgf {
+
+// Number of BF16 slices per operand.  A value x in a row (or column) whose
+// largest entry is below 2^e is written as x = 2^e * sum_s q_s 2^(-7-8s),
+// s = 0..5, with integers |q_s| <= 128 (8 significant bits, exact in BF16).
+constexpr int kSlices = 6;
+
+// Products kept: slice pairs (i, j) with i + j <= kSlices - 1 (21 pairs).
+// Pair (i, j) lands in accumulator min(i + j, kGroups - 1).  Every partial
+// sum of group g = i + j is an integer multiple of that group's unit
+// 2^(-14-8g) sigma_row sigma_col, at most (g+1) 2^14 K units, so the FP32
+// accumulation of groups 0..3 is exact (worst case: all slices at full
+// magnitude with equal signs) up to K = 1024, 512, 341 and 256 real terms,
+// and in practice far beyond.  The last accumulator collects the tail
+// g = 4, 5, whose products are not all integers in one unit: the tensor
+// core truncates their low bits, an error of order K * 11 * 2^-56 of the
+// leading term.  (Folding g = 3 into the tail as well would cost ~2^-35 at
+// K = 512, which is why five accumulators are kept.)
+constexpr int kGroups = 5;
+
+// Row pitch of a slice matrix in BF16 elements: real K = 2 k (re/im
+// interleaved) rounded up to a multiple of 64 so every 64-element chunk is
+// full; the padding is zero.
+inline int slice_pitch(int k) { return ((2 * k + 63) / 64) * 64; }
+
+// Slices of the left operand A (m x k complex, df):
+//   out[((bi*kSlices + s)*m + r)*Kp + 2j + {0,1}] = slice s of (Re, Im) A[r][j]
+rgf_status slice_rows(int batch, int m, int k, const float4* A, long sA, __nv_bfloat16* out, int Kp,
+                      const int* active, cudaStream_t st);
+// Slices of the right operand B (k x n complex, df) in transposed,
+// complex-expanded form (2n rows of Kp):
+//   row 2c  : (Re B[j][c], -Im B[j][c]) at K positions (2j, 2j+1)
+//   row 2c+1: (Im B[j][c],  Re B[j][c])
+// so that one real GEMM gives Re C in real column 2c and Im C in 2c+1.
+// colexp is int scratch of batch*n entries.
+rgf_status slice_cols(int batch, int k, int n, const float4* B, long sB, __nv_bfloat16* out, int Kp,
+                      int* colexp, const int* active, cudaStream_t st);
+
+struct OzGemm {
+    int batch, m, n, k;          // complex sizes: C (m x n) = A (m x k) B (k x n)
+    const __nv_bfloat16* As;     // [batch][kSlices][m][Kp]
+    const __nv_bfloat16* Bs;     // [batch][kSlices][2n][Kp]
+    int Kp;
+    float alpha;                 // +1 or -1
+    const float4* D; long sD;    // optional addend (may alias C)
+    int add_identity;            // C += I
+    float4* C; long sC;
+    const int* active;
+    int* status;                 // device word, nonzero after a pipeline timeout
+};
+
+// Reference core on the legacy warp-level tensor path (mma.sync BF16).
+rgf_status oz_gemm_mma(const OzGemm& g, cudaStream_t st);
+// Blackwell core: TMA -> shared memory -> tcgen05.mma -> TMEM accumulators.
+rgf_status oz_gemm_tc(const OzGemm& g, cudaStream_t st);
+// Which core oz_gemm uses (0 = tcgen05, 1 = mma.sync); set by the plan.
+rgf_status oz_gemm(const OzGemm& g, int core, cudaStream_t st);
+
+// Elementwise df kernels (batch of b x b matrices, stride b*b unless noted).
+rgf_status to_dfc(long n, const double2* src, float4* dst, cudaStream_t st);
+// out[s*W+e] = z_e S' - H' - sub[s*W+e] in df arithmetic; S, H df blocks.
+struct FormSrcDf {
+    const float4* S[2];
+    const float4* H[2];
+    int trans[2];
+};
+rgf_status form_dfc(int W, int nsrc, int b, const double* E, double eta, const FormSrcDf& src, float4* out,
+                    const float4* sub, const int* active, cudaStream_t st);
+rgf_status dfc_hi_to_c64(int batch, int b, const float4* X, float2* Y, const int* active, cudaStream_t st);
+rgf_status c64_to_dfc(int batch, int b, const float2* X, float4* Y, const int* active, cudaStream_t st);
+rgf_status copy_dfc(int batch, int b, float4* dst, const float4* src, const int* active, cudaStream_t st);
+rgf_status set_identity_dfc(int batch, int b, float4* A, cudaStream_t st);
+rgf_status dec_update_dfc(int batch, int b, float4* eps_s, float4* eps, const float4* agb, const float4* bga,
+                          const int* active, cudaStream_t st);
+rgf_status dec_check_dfc(int batch, int b, const float4* alpha, const float4* beta, const double* anorm, double tol,
+                         int it, int* active, int* iters, int* remaining, cudaStream_t st);
+rgf_status fro_norm_dfc(int batch, int b, const float4* A, double* out, cudaStream_t st);
+rgf_status gamma_dfc(int batch, int b, const float4* sigma, float4* gamma, cudaStream_t st);
+rgf_status axpy_dfc(int batch, int b, float alpha, const float4* X, float4* Y, cudaStream_t st);
+// Newton-Schulz bookkeeping for step s of at most max_steps on batch
+// entries i (energy e = i mod W), given R = I - M X:
+//   err[e] = max(err[e], |R_i|_F);
+//   on step 0, entries with |R_i|_F >= 0.5 (or not finite) get bad[i] = 1,
+//     are counted in *bad_count and flagged RGF_FLAG_REFINE (their FP32
+//     seed does not contract; the caller reseeds them in FP64);
+//   next_act[i] = act[i] && |R_i|_F > 3e-7 (after this step's correction
+//     the residual is below |R_i|^2 <= 1e-13, so the entry is done);
+//   on the last step an entry still above 3e-7 is flagged RGF_FLAG_REFINE.
+rgf_status ns_check(int batch, int W, int b, const float4* R, double* err, int* flags, int step, int max_steps,
+                    const int* act, int* next_act, int* bad, int* bad_count, cudaStream_t st);
+// out[i] = act ? act[i] : 1
+rgf_status mask_init(int batch, const int* act, int* out, cudaStream_t st);
+// Masked conversions between df and FP64 complex (entries with mask[i]).
+rgf_status dfc_to_c128(int batch, int b, const float4* X, double2* Y, const int* mask, cudaStream_t st);
+rgf_status c128_to_dfc(int batch, int b, const double2* X, float4* Y, const int* mask, cudaStream_t st);
+// T[i] = Re sum X_jk conj(Y_jk) reduced in FP64 from df inputs.
+rgf_status trace_dfc(int batch, int b, const float4* X, const float4* Y, double* T, double* Ti, cudaStream_t st);
+
+}  // namespace rgf

@@ -1,0 +1,392 @@
+// Mixed-precision RGF path.  Every complex GEMM is an exact BF16 slice
+// product on the tensor cores with a double-float (about 48-bit) result;
+// every inverse is an FP32 Gauss-Jordan seed refined by Newton-Schulz steps
+// X <- X + X (I - M X) whose residual and correction are again slice
+// products.  Matrices between kernels are double-float complex (float4).
+// The final Caroli trace is reduced in FP64.
+#include <utility>
+#include <vector>
+
+#include "gj_tmpl.cuh"
+#include "mixed.h"
+#include "plan.h"
+
+namespace rgf {
+
+namespace {
+constexpr int kPoolUnits = 24;  // df matrices, in units of W
+
+struct MixedState {
+    int b = 0, W = 0, Kp = 0;
+    float4* H_diag = nullptr;
+    float4* S_diag = nullptr;
+    float4* H_lower = nullptr;
+    float4* S_lower = nullptr;
+    float4* lead[2][6] = {};
+    float4* pool = nullptr;
+    __nv_bfloat16* sa[2] = {};
+    __nv_bfloat16* sb[2] = {};
+    int* colexp = nullptr;
+    float2* c64 = nullptr;
+    void* inv_ws = nullptr;
+    int* status = nullptr;
+    int* nsact[2] = {};
+    int* bad = nullptr;
+    int* bad_count = nullptr;
+    int* h_bad = nullptr;   // pinned
+    double2* c128 = nullptr;
+    void* inv64_ws = nullptr;
+    int core = 0;
+};
+
+size_t sa_bytes(int cnt, int b, int Kp) { return (size_t)cnt * kSlices * b * Kp * sizeof(__nv_bfloat16); }
+size_t sb_bytes(int cnt, int b, int Kp) { return (size_t)cnt * kSlices * 2 * b * Kp * sizeof(__nv_bfloat16); }
+
+struct Ctx {
+    MixedState* m;
+    rgf_plan_s* p;
+    cudaStream_t st;
+    long nn;
+    int b;
+};
+
+// Slice A by rows into sa[ia], B by columns into sb[ib].
+rgf_status sliceA(const Ctx& c, int cnt, int ia, const float4* A, const int* act) {
+    return slice_rows(cnt, c.b, c.b, A, c.nn, c.m->sa[ia], c.m->Kp, act, c.st);
+}
+rgf_status sliceB(const Ctx& c, int cnt, int ib, const float4* B, const int* act) {
+    return slice_cols(cnt, c.b, c.b, B, c.nn, c.m->sb[ib], c.m->Kp, c.m->colexp, act, c.st);
+}
+// C = alpha * A B (+ D) (+ I) from already sliced operands.
+rgf_status mm(const Ctx& c, int cnt, int ia, int ib, float alpha, const float4* D, int addI, float4* C,
+              const int* act) {
+    OzGemm g{};
+    g.batch = cnt;
+    g.m = g.n = g.k = c.b;
+    g.As = c.m->sa[ia];
+    g.Bs = c.m->sb[ib];
+    g.Kp = c.m->Kp;
+    g.alpha = alpha;
+    g.D = D;
+    g.sD = c.nn;
+    g.add_identity = addI;
+    g.C = C;
+    g.sC = c.nn;
+    g.active = act;
+    g.status = c.m->status;
+    return oz_gemm(g, c.m->core, c.st);
+}
+
+// X = M^-1 for cnt matrices (batch entries i, energy i mod W): an FP32
+// Gauss-Jordan seed, then up to ns_steps Newton-Schulz steps X += X (I - M X)
+// in place, each entry stopping once its residual predicts convergence.
+// Entries whose FP32 seed does not contract (|I - M X|_F >= 0.5) are
+// reseeded with the FP64 Gauss-Jordan inverse before the first correction.
+// Uses sa[1] for M, sa[0]/sb[0] for the steps and R as df scratch.
+rgf_status inv_mixed(const Ctx& c, int cnt, int W, const float4* M, float4* X, float4* R, const int* act,
+                     int* gj_flags) {
+    MixedState* m = c.m;
+    rgf_plan_s* p = c.p;
+    RGF_TRY(dfc_hi_to_c64(cnt, c.b, M, m->c64, act, c.st));
+    RGF_TRY(inv_t<float2>(cnt, c.b, m->c64, c.nn, m->inv_ws, gj_flags, act, c.st));
+    RGF_TRY(c64_to_dfc(cnt, c.b, m->c64, X, act, c.st));
+    const int steps = p->opt.ns_steps;
+    if (steps == 0) return RGF_OK;
+    int* cur = m->nsact[0];
+    int* nxt = m->nsact[1];
+    RGF_TRY(mask_init(cnt, act, cur, c.st));
+    RGF_TRY(sliceA(c, cnt, 1, M, act));
+    for (int s = 0; s < steps; ++s) {
+        RGF_TRY(sliceB(c, cnt, 0, X, cur));
+        RGF_TRY(mm(c, cnt, 1, 0, -1.0f, nullptr, 1, R, cur));  // R = I - M X
+        if (s == 0) RGF_CUDA_TRY(cudaMemsetAsync(m->bad_count, 0, sizeof(int), c.st));
+        RGF_TRY(ns_check(cnt, W, c.b, R, p->d_err, p->d_flags, s, steps, cur, nxt, m->bad, m->bad_count, c.st));
+        if (s == 0) {
+            RGF_CUDA_TRY(cudaMemcpyAsync(m->h_bad, m->bad_count, sizeof(int), cudaMemcpyDeviceToHost, c.st));
+            RGF_CUDA_TRY(cudaStreamSynchronize(c.st));
+            if (*m->h_bad > 0) {
+                p->n_reseeds += *m->h_bad;
+                RGF_TRY(dfc_to_c128(cnt, c.b, M, m->c128, m->bad, c.st));
+                RGF_TRY(inv_t<double2>(cnt, c.b, m->c128, c.nn, m->inv64_ws, gj_flags, m->bad, c.st));
+                RGF_TRY(c128_to_dfc(cnt, c.b, m->c128, X, m->bad, c.st));
+                RGF_TRY(sliceB(c, cnt, 0, X, m->bad));
+                RGF_TRY(mm(c, cnt, 1, 0, -1.0f, nullptr, 1, R, m->bad));
+            }
+        }
+        RGF_TRY(sliceA(c, cnt, 0, X, cur));
+        RGF_TRY(sliceB(c, cnt, 0, R, cur));
+        RGF_TRY(mm(c, cnt, 0, 0, 1.0f, X, 0, X, cur));  // X += X R
+        std::swap(cur, nxt);
+    }
+    return RGF_OK;
+}
+}  // namespace
+
+size_t mixed_workspace_bytes(int W, int b) {
+    const int Kp = slice_pitch(b);
+    const size_t nn = (size_t)b * b;
+    size_t s = (size_t)kPoolUnits * W * nn * sizeof(float4);
+    s += 2 * sa_bytes(2 * W, b, Kp) + 2 * sb_bytes(2 * W, b, Kp);
+    s += (size_t)2 * W * nn * sizeof(float2) + inv_workspace_bytes_t<float2>(2 * W, b);
+    s += (size_t)2 * W * nn * sizeof(double2) + inv_workspace_bytes_t<double2>(2 * W, b);
+    s += (size_t)2 * W * b * sizeof(int) + (size_t)2 * W * 3 * sizeof(int) + 8192;
+    return s;
+}
+
+rgf_status mixed_init(rgf_plan_s* p) {
+    auto* m = new MixedState();
+    p->mixed = m;
+    m->b = p->b;
+    m->W = p->W;
+    m->Kp = slice_pitch(p->b);
+    const int b = p->b, W = p->W, N = p->N;
+    const size_t nn = (size_t)b * b;
+    const char* env = getenv("RGF_OZ_CORE");
+    m->core = (env && env[0] == '1') ? 1 : 0;
+    auto alloc = [&](void** ptr, size_t bytes) -> rgf_status {
+        if (cudaMalloc(ptr, bytes ? bytes : 16) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("mixed_init: cudaMalloc(%zu) failed", bytes);
+            return RGF_E_OOM;
+        }
+        return RGF_OK;
+    };
+    RGF_TRY(alloc((void**)&m->H_diag, nn * N * sizeof(float4)));
+    RGF_TRY(alloc((void**)&m->S_diag, nn * N * sizeof(float4)));
+    if (N > 1) {
+        RGF_TRY(alloc((void**)&m->H_lower, nn * (N - 1) * sizeof(float4)));
+        RGF_TRY(alloc((void**)&m->S_lower, nn * (N - 1) * sizeof(float4)));
+    }
+    for (int s = 0; s < 2; ++s)
+        for (int k = 0; k < 6; ++k) RGF_TRY(alloc((void**)&m->lead[s][k], nn * sizeof(float4)));
+    // Carve the workspace.
+    char* w = (char*)p->ws;
+    m->pool = (float4*)w;
+    w += (size_t)kPoolUnits * W * nn * sizeof(float4);
+    for (int i = 0; i < 2; ++i) {
+        m->sa[i] = (__nv_bfloat16*)w;
+        w += sa_bytes(2 * W, b, m->Kp);
+    }
+    for (int i = 0; i < 2; ++i) {
+        m->sb[i] = (__nv_bfloat16*)w;
+        w += sb_bytes(2 * W, b, m->Kp);
+    }
+    m->c64 = (float2*)w;
+    w += (size_t)2 * W * nn * sizeof(float2);
+    m->inv_ws = (void*)w;
+    w += inv_workspace_bytes_t<float2>(2 * W, b);
+    w = (char*)(((uintptr_t)w + 255) & ~(uintptr_t)255);
+    m->c128 = (double2*)w;
+    w += (size_t)2 * W * nn * sizeof(double2);
+    m->inv64_ws = (void*)w;
+    w += inv_workspace_bytes_t<double2>(2 * W, b);
+    w = (char*)(((uintptr_t)w + 255) & ~(uintptr_t)255);
+    m->nsact[0] = (int*)w;
+    w += (size_t)2 * W * sizeof(int);
+    m->nsact[1] = (int*)w;
+    w += (size_t)2 * W * sizeof(int);
+    m->bad = (int*)w;
+    w += (size_t)2 * W * sizeof(int);
+    w = (char*)(((uintptr_t)w + 255) & ~(uintptr_t)255);
+    m->colexp = (int*)w;
+    // Zero the slice buffers once: the K padding is never written again.
+    RGF_CUDA_TRY(cudaMemsetAsync(m->sa[0], 0, 2 * sa_bytes(2 * W, b, m->Kp) + 2 * sb_bytes(2 * W, b, m->Kp),
+                                 p->stream));
+    RGF_TRY(alloc((void**)&m->status, sizeof(int)));
+    RGF_TRY(alloc((void**)&m->bad_count, sizeof(int)));
+    if (cudaMallocHost((void**)&m->h_bad, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("mixed_init: cudaMallocHost failed");
+        return RGF_E_OOM;
+    }
+    RGF_CUDA_TRY(cudaMemsetAsync(m->status, 0, sizeof(int), p->stream));
+    RGF_CUDA_TRY(cudaStreamSynchronize(p->stream));
+    return RGF_OK;
+}
+
+void mixed_free(rgf_plan_s* p) {
+    auto* m = (MixedState*)p->mixed;
+    if (!m) return;
+    cudaFree(m->H_diag);
+    cudaFree(m->S_diag);
+    cudaFree(m->H_lower);
+    cudaFree(m->S_lower);
+    for (int s = 0; s < 2; ++s)
+        for (int k = 0; k < 6; ++k) cudaFree(m->lead[s][k]);
+    cudaFree(m->status);
+    cudaFree(m->bad_count);
+    if (m->h_bad) cudaFreeHost(m->h_bad);
+    delete m;
+    p->mixed = nullptr;
+}
+
+rgf_status mixed_on_blocks(rgf_plan_s* p) {
+    auto* m = (MixedState*)p->mixed;
+    const long nn = (long)p->b * p->b;
+    RGF_TRY(to_dfc(nn * p->N, p->H_diag, m->H_diag, p->stream));
+    RGF_TRY(to_dfc(nn * p->N, p->S_diag, m->S_diag, p->stream));
+    if (p->N > 1) {
+        RGF_TRY(to_dfc(nn * (p->N - 1), p->H_lower, m->H_lower, p->stream));
+        RGF_TRY(to_dfc(nn * (p->N - 1), p->S_lower, m->S_lower, p->stream));
+    }
+    RGF_CUDA_TRY(cudaStreamSynchronize(p->stream));
+    return RGF_OK;
+}
+
+rgf_status mixed_on_lead(rgf_plan_s* p, int side) {
+    auto* m = (MixedState*)p->mixed;
+    const long nn = (long)p->b * p->b;
+    for (int k = 0; k < 6; ++k) RGF_TRY(to_dfc(nn, p->lead[side][k], m->lead[side][k], p->stream));
+    RGF_CUDA_TRY(cudaStreamSynchronize(p->stream));
+    return RGF_OK;
+}
+
+rgf_status mixed_wave(rgf_plan_s* p, int W) {
+    auto* m = (MixedState*)p->mixed;
+    cudaStream_t st = p->stream;
+    const int b = p->b, N = p->N;
+    const long nn = (long)b * b;
+    const double eta = p->opt.eta;
+    const double* E = p->d_E;
+    Ctx c{m, p, st, nn, b};
+    auto U = [&](int unit) { return m->pool + (long)unit * W * nn; };
+    const int W2 = 2 * W;
+
+    RGF_CUDA_TRY(cudaMemsetAsync(p->d_flags, 0, sizeof(int) * W, st));
+    RGF_CUDA_TRY(cudaMemsetAsync(p->d_dec_flags, 0, sizeof(int) * W2, st));
+    RGF_CUDA_TRY(cudaMemsetAsync(p->d_err, 0, sizeof(double) * W, st));
+    RGF_CUDA_TRY(cudaMemsetAsync(m->status, 0, sizeof(int), st));
+
+    // ---------------------------------------------------------- decimation
+    float4 *eps_s = U(0), *eps = U(2), *alpha = U(4), *beta = U(6), *g = U(8), *ga = U(10), *gb = U(12);
+    float4 *t1 = U(14), *t2 = U(16), *t3 = U(18), *t4 = U(20), *R = U(22);
+    float4** L = m->lead[0];
+    float4** Rl = m->lead[1];
+    {
+        FormSrcDf a{{L[1], Rl[1]}, {L[0], Rl[0]}, {0, 0}};
+        RGF_TRY(form_dfc(W, 2, b, E, eta, a, eps, nullptr, nullptr, st));
+        RGF_TRY(copy_dfc(W2, b, eps_s, eps, nullptr, st));
+        FormSrcDf al{{L[3], Rl[3]}, {L[2], Rl[2]}, {0, 1}};
+        FormSrcDf be{{L[3], Rl[3]}, {L[2], Rl[2]}, {1, 0}};
+        RGF_TRY(form_dfc(W, 2, b, E, eta, al, alpha, nullptr, nullptr, st));
+        RGF_TRY(form_dfc(W, 2, b, E, eta, be, beta, nullptr, nullptr, st));
+        RGF_TRY(fro_norm_dfc(W2, b, eps, p->d_anorm, st));
+    }
+    {
+        std::vector<int> ones(W2, 1);
+        RGF_CUDA_TRY(cudaMemcpyAsync(p->d_active, ones.data(), sizeof(int) * W2, cudaMemcpyHostToDevice, st));
+        RGF_CUDA_TRY(cudaMemsetAsync(p->d_iters, 0, sizeof(int) * W2, st));
+        int* act = p->d_active;
+        for (int it = 1; it <= p->opt.dec_max_iter; ++it) {
+            RGF_TRY(inv_mixed(c, W2, W, eps, g, R, act, p->d_dec_flags));
+            RGF_TRY(sliceA(c, W2, 0, g, act));
+            RGF_TRY(sliceB(c, W2, 0, alpha, act));
+            RGF_TRY(mm(c, W2, 0, 0, 1.0f, nullptr, 0, ga, act));  // g alpha
+            RGF_TRY(sliceB(c, W2, 1, beta, act));
+            RGF_TRY(mm(c, W2, 0, 1, 1.0f, nullptr, 0, gb, act));  // g beta
+            RGF_TRY(sliceB(c, W2, 0, gb, act));
+            RGF_TRY(sliceB(c, W2, 1, ga, act));
+            RGF_TRY(sliceA(c, W2, 0, alpha, act));
+            RGF_TRY(mm(c, W2, 0, 0, 1.0f, nullptr, 0, t1, act));   // alpha g beta
+            RGF_TRY(mm(c, W2, 0, 1, -1.0f, nullptr, 0, t3, act));  // -alpha g alpha
+            RGF_TRY(sliceA(c, W2, 0, beta, act));
+            RGF_TRY(mm(c, W2, 0, 1, 1.0f, nullptr, 0, t2, act));   // beta g alpha
+            RGF_TRY(mm(c, W2, 0, 0, -1.0f, nullptr, 0, t4, act));  // -beta g beta
+            RGF_TRY(dec_update_dfc(W2, b, eps_s, eps, t1, t2, act, st));
+            std::swap(alpha, t3);
+            std::swap(beta, t4);
+            RGF_CUDA_TRY(cudaMemsetAsync(p->d_remaining, 0, sizeof(int), st));
+            RGF_TRY(dec_check_dfc(W2, b, alpha, beta, p->d_anorm, p->opt.dec_tol, it, act, p->d_iters,
+                                  p->d_remaining, st));
+            RGF_CUDA_TRY(cudaMemcpyAsync(p->h_remaining, p->d_remaining, sizeof(int), cudaMemcpyDeviceToHost, st));
+            RGF_CUDA_TRY(cudaStreamSynchronize(st));
+            if (*p->h_remaining == 0) break;
+        }
+        RGF_TRY(merge_dec_flags(W, p->d_dec_flags, p->d_active, p->d_flags, st));
+        RGF_TRY(inv_mixed(c, W2, W, eps_s, g, R, nullptr, p->d_dec_flags));
+        RGF_TRY(merge_dec_flags(W, p->d_dec_flags, p->d_active, p->d_flags, st));
+    }
+
+    // ---------------------------------------------------------- self-energies
+    float4* sigma = U(0);
+    float4* gamma = U(2);
+    {
+        FormSrcDf x1{{L[5], Rl[5]}, {L[4], Rl[4]}, {0, 1}};
+        FormSrcDf x2{{L[5], Rl[5]}, {L[4], Rl[4]}, {1, 0}};
+        RGF_TRY(form_dfc(W, 2, b, E, eta, x1, t1, nullptr, nullptr, st));
+        RGF_TRY(form_dfc(W, 2, b, E, eta, x2, t2, nullptr, nullptr, st));
+        RGF_TRY(sliceA(c, W2, 0, t1, nullptr));
+        RGF_TRY(sliceB(c, W2, 0, g, nullptr));
+        RGF_TRY(mm(c, W2, 0, 0, 1.0f, nullptr, 0, t3, nullptr));
+        RGF_TRY(sliceA(c, W2, 0, t3, nullptr));
+        RGF_TRY(sliceB(c, W2, 0, t2, nullptr));
+        RGF_TRY(mm(c, W2, 0, 0, 1.0f, nullptr, 0, sigma, nullptr));
+        RGF_TRY(gamma_dfc(W2, b, sigma, gamma, st));
+    }
+    float4* sigL = sigma;
+    float4* sigR = sigma + (long)W * nn;
+    float4* gamL = gamma;
+    float4* gamR = gamma + (long)W * nn;
+
+    // ---------------------------------------------------------- sweep
+    float4 *gi = U(4), *P = U(5), *M = U(6), *Lt = U(7), *Ut = U(8), *Q = U(9), *Qn = U(10);
+    float4 *G = U(11), *Xt = U(12), *Yt = U(13), *Rs = U(14);
+    if (N == 1) {
+        FormSrcDf a0{{m->S_diag, nullptr}, {m->H_diag, nullptr}, {0, 0}};
+        RGF_TRY(form_dfc(W, 1, b, E, eta, a0, M, sigL, nullptr, st));
+        RGF_TRY(axpy_dfc(W, b, -1.0f, sigR, M, st));
+        RGF_TRY(inv_mixed(c, W, W, M, gi, Rs, nullptr, p->d_flags));
+        G = gi;
+    } else {
+        FormSrcDf a0{{m->S_diag, nullptr}, {m->H_diag, nullptr}, {0, 0}};
+        RGF_TRY(form_dfc(W, 1, b, E, eta, a0, M, sigL, nullptr, st));
+        RGF_TRY(inv_mixed(c, W, W, M, gi, Rs, nullptr, p->d_flags));
+        for (int i = 1; i < N; ++i) {
+            const float4* Sl = m->S_lower + (long)(i - 1) * nn;
+            const float4* Hl = m->H_lower + (long)(i - 1) * nn;
+            FormSrcDf up{{Sl, nullptr}, {Hl, nullptr}, {1, 0}};
+            FormSrcDf lo{{Sl, nullptr}, {Hl, nullptr}, {0, 0}};
+            FormSrcDf ai{{m->S_diag + (long)i * nn, nullptr}, {m->H_diag + (long)i * nn, nullptr}, {0, 0}};
+            RGF_TRY(form_dfc(W, 1, b, E, eta, up, Ut, nullptr, nullptr, st));
+            RGF_TRY(form_dfc(W, 1, b, E, eta, lo, Lt, nullptr, nullptr, st));
+            RGF_TRY(form_dfc(W, 1, b, E, eta, ai, M, (i == N - 1) ? sigR : nullptr, nullptr, st));
+            RGF_TRY(sliceA(c, W, 0, gi, nullptr));
+            RGF_TRY(sliceB(c, W, 0, Ut, nullptr));
+            RGF_TRY(mm(c, W, 0, 0, -1.0f, nullptr, 0, P, nullptr));  // P = -g tau'
+            RGF_TRY(sliceA(c, W, 0, Lt, nullptr));
+            RGF_TRY(sliceB(c, W, 0, P, nullptr));
+            RGF_TRY(mm(c, W, 0, 0, 1.0f, M, 0, M, nullptr));  // M += tau P
+            if (i == 1) {
+                std::swap(Q, P);
+            } else {
+                RGF_TRY(sliceA(c, W, 1, Q, nullptr));
+                RGF_TRY(mm(c, W, 1, 0, 1.0f, nullptr, 0, Qn, nullptr));  // Q P
+                std::swap(Q, Qn);
+            }
+            RGF_TRY(inv_mixed(c, W, W, M, gi, Rs, nullptr, p->d_flags));
+        }
+        RGF_TRY(sliceA(c, W, 0, Q, nullptr));
+        RGF_TRY(sliceB(c, W, 0, gi, nullptr));
+        RGF_TRY(mm(c, W, 0, 0, 1.0f, nullptr, 0, G, nullptr));
+    }
+
+    // ---------------------------------------------------------- Caroli trace
+    RGF_TRY(sliceA(c, W, 0, gamL, nullptr));
+    RGF_TRY(sliceB(c, W, 0, G, nullptr));
+    RGF_TRY(mm(c, W, 0, 0, 1.0f, nullptr, 0, Xt, nullptr));
+    RGF_TRY(sliceA(c, W, 0, G, nullptr));
+    RGF_TRY(sliceB(c, W, 0, gamR, nullptr));
+    RGF_TRY(mm(c, W, 0, 0, 1.0f, nullptr, 0, Yt, nullptr));
+    RGF_TRY(trace_dfc(W, b, Xt, Yt, p->d_T, p->d_Ti, st));
+
+    int h_status = 0;
+    RGF_CUDA_TRY(cudaMemcpyAsync(&h_status, m->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    RGF_CUDA_TRY(cudaStreamSynchronize(st));
+    if (h_status != 0) {
+        set_error("tensor-core GEMM pipeline timed out (status 0x%x)", h_status);
+        return RGF_E_CUDA;
+    }
+    return RGF_OK;
+}
+
+}  // namespace rgf

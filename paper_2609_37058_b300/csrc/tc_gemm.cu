@@ -1,0 +1,339 @@
+// Slice-product complex GEMM on the Blackwell tensor cores (sm_103a).
+//
+// One CTA computes a 128 x 96 tile of the real output (128 rows, 48
+// complex columns as interleaved re/im pairs) of one batch entry:
+//   * TMA (cp.async.bulk.tensor, 64-byte swizzle) brings, per 32-element K
+//     chunk, the six BF16 slices of the A rows and of the B columns into
+//     shared memory; two stages, 84 KB each;
+//   * one thread issues tcgen05.mma (kind::f16, BF16 x BF16 -> FP32,
+//     M = 128, N = 96, K = 16) for the 21 slice pairs (i, j), i + j <= 5,
+//     accumulating pair (i, j) in TMEM accumulator min(i + j, 4) (five
+//     accumulators x 96 columns of the 512 allocated);
+//   * four warps read the accumulators back with tcgen05.ld and combine
+//     the groups into double-float results (TwoSum), apply the epilogue
+//     (sign, addend, identity) and store float4 (re_hi, re_lo, im_hi, im_lo).
+// Every wait on an mbarrier is bounded (2 s); a timeout sets a status bit
+// that the host turns into an error, and the CTA still releases its TMEM.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "df.cuh"
+#include "metrics.h"
+#include "mixed.h"
+
+namespace rgf {
+
+namespace {
+constexpr int TC_BM = 128, TC_BN = 96, TC_BK = 32;  // BK in BF16 elements (64 bytes)
+constexpr int TC_STAGES = 2;
+constexpr int TC_ATILE = TC_BM * TC_BK * 2;                      // 8 KB per A slice tile
+constexpr int TC_BTILE = TC_BN * TC_BK * 2;                      // 6 KB per B slice tile
+constexpr int TC_STAGE_BYTES = kSlices * (TC_ATILE + TC_BTILE);  // 84 KB
+constexpr int TC_SMEM = TC_STAGES * TC_STAGE_BYTES + 1024 + 256;
+constexpr uint32_t TC_TMEM_COLS = 512;
+constexpr unsigned long long TC_WAIT_NS = 2000000000ull;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: true when the phase completed, false (and status |= code)
+// after TC_WAIT_NS nanoseconds.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* status, int code) {
+    if (mbar_try(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer();
+    for (unsigned it = 1;; ++it) {
+        if (mbar_try(bar, parity)) return true;
+        if ((it & 255u) == 0 && globaltimer() - t0 > TC_WAIT_NS) {
+            atomicOr(status, code);
+            return false;
+        }
+    }
+}
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y, int z, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+        : "memory");
+}
+// Shared-memory matrix descriptor: K-major tile, rows of 64 bytes with the
+// 64-byte swizzle, 8-row groups 512 bytes apart.
+__device__ __forceinline__ uint64_t desc_sw64(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;              // leading byte offset (unused for this layout)
+    d |= (uint64_t)(512u >> 4) << 32;    // stride byte offset
+    d |= (uint64_t)1 << 46;              // descriptor version
+    d |= (uint64_t)4 << 61;              // 64-byte swizzle
+    return d;
+}
+// Instruction descriptor: D = F32, A = B = BF16, both K-major, N = 96, M = 128.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_BN >> 3) << 17) |
+                            ((uint32_t)(TC_BM >> 4) << 24);
+
+__device__ __forceinline__ void umma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accum) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(kIdesc), "r"(accum));
+}
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Groups 0..3 through exact TwoSums, the tail into the low word.
+__device__ __forceinline__ float2 combine5(float g0, float g1, float g2, float g3, float g4) {
+    const float2 s = two_sum(g0, g1);
+    const float2 t = two_sum(s.x, g2);
+    const float2 u = two_sum(t.x, g3);
+    float lo = s.y + t.y;
+    lo += u.y;
+    lo += g4;
+    return fast_two_sum(u.x, lo);
+}
+}  // namespace
+
+__global__ void __launch_bounds__(128, 1)
+    k_oz_tc(OzGemm g, const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB) {
+    const int bi = blockIdx.z;
+    if (g.active && !g.active[bi]) return;
+    extern __shared__ __align__(1024) unsigned char smem_tc[];
+    unsigned char* base = (unsigned char*)(((uintptr_t)smem_tc + 1023) & ~(uintptr_t)1023);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(base + TC_STAGES * TC_STAGE_BYTES);
+    // bars[0..1] full, bars[2..3] empty, bars[4] done; slot after them
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 8);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.y * TC_BM, n0 = blockIdx.x * TC_BN;
+    const int nk = g.Kp / TC_BK;
+    int* status = g.status;
+
+    if (tid == 0) {
+        for (int i = 0; i < 5; ++i) mbar_init(smem_u32(&bars[i]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(TC_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t taddr = *tmem_slot;
+
+    if (tid == 0) {
+        // ---------------- TMA producer
+        for (int kc = 0; kc < nk; ++kc) {
+            const int s = kc & 1;
+            if (kc >= TC_STAGES) {
+                if (!mbar_wait(smem_u32(&bars[2 + s]), ((kc >> 1) - 1) & 1, status, 0x1)) break;
+            }
+            const uint32_t fb = smem_u32(&bars[s]);
+            mbar_expect_tx(fb, TC_STAGE_BYTES);
+            unsigned char* st = base + s * TC_STAGE_BYTES;
+#pragma unroll
+            for (int sl = 0; sl < kSlices; ++sl) {
+                tma_load_3d(smem_u32(st + sl * TC_ATILE), &tmA, kc * TC_BK, m0, bi * kSlices + sl, fb);
+                tma_load_3d(smem_u32(st + kSlices * TC_ATILE + sl * TC_BTILE), &tmB, kc * TC_BK, n0,
+                            bi * kSlices + sl, fb);
+            }
+        }
+    } else if (tid == 32) {
+        // ---------------- MMA issuer
+        bool ok = true;
+        for (int kc = 0; kc < nk && ok; ++kc) {
+            const int s = kc & 1;
+            if (!mbar_wait(smem_u32(&bars[s]), (kc >> 1) & 1, status, 0x2)) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            unsigned char* st = base + s * TC_STAGE_BYTES;
+            const uint32_t a0 = smem_u32(st), b0 = smem_u32(st + kSlices * TC_ATILE);
+            uint32_t started = 0;
+#pragma unroll
+            for (int i = 0; i < kSlices; ++i) {
+#pragma unroll
+                for (int j = 0; j < kSlices; ++j) {
+                    if (i + j > kSlices - 1) continue;
+                    const int grp = (i + j) < (kGroups - 1) ? (i + j) : (kGroups - 1);
+#pragma unroll
+                    for (int kk = 0; kk < TC_BK / 16; ++kk) {
+                        const uint64_t ad = desc_sw64(a0 + i * TC_ATILE + kk * 32);
+                        const uint64_t bd = desc_sw64(b0 + j * TC_BTILE + kk * 32);
+                        const uint32_t acc = (kc > 0 || (started >> grp) & 1u) ? 1u : 0u;
+                        umma(taddr + (uint32_t)(grp * TC_BN), ad, bd, acc);
+                        started |= 1u << grp;
+                    }
+                }
+            }
+            umma_commit(smem_u32(&bars[2 + s]));
+        }
+        umma_commit(smem_u32(&bars[4]));
+    }
+    __syncwarp();
+
+    // ---------------- epilogue: TMEM -> registers -> df -> global
+    // One lane per warp waits; the outcome is made warp-uniform because the
+    // TMEM loads below are warp-collective.
+    int done_i = 0;
+    if (lane == 0) done_i = mbar_wait(smem_u32(&bars[4]), 0, status, 0x4) ? 1 : 0;
+    const bool done = __shfl_sync(0xffffffffu, done_i, 0) != 0;
+    __syncwarp();
+    tc_fence_after();
+    if (done) {
+        const int r = m0 + warp * 32 + lane;
+        const uint32_t trow = taddr + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+        for (int q = 0; q < TC_BN / 16; ++q) {
+            float v[kGroups][16];
+#pragma unroll
+            for (int gq = 0; gq < kGroups; ++gq) tmem_ld16(trow + gq * TC_BN + q * 16, v[gq]);
+            tmem_ld_wait();
+            if (r < g.m) {
+                const int c0 = (n0 + q * 16) >> 1;
+                float4* out = g.C + (long)bi * g.sC + (long)r * g.n;
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    const int c = c0 + t;
+                    if (c < g.n) {
+                        float2 re = combine5(v[0][2 * t], v[1][2 * t], v[2][2 * t], v[3][2 * t], v[4][2 * t]);
+                        float2 im = combine5(v[0][2 * t + 1], v[1][2 * t + 1], v[2][2 * t + 1], v[3][2 * t + 1],
+                                             v[4][2 * t + 1]);
+                        if (g.alpha < 0.0f) {
+                            re = df_neg(re);
+                            im = df_neg(im);
+                        }
+                        if (g.D) {
+                            const float4 d = g.D[(long)bi * g.sD + (long)r * g.n + c];
+                            re = df_add(re, re_of(d));
+                            im = df_add(im, im_of(d));
+                        }
+                        if (g.add_identity && r == c) re = df_add(re, make_float2(1.0f, 0.0f));
+                        out[c] = cdf(re, im);
+                    }
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (!done && tid == 0) {
+        // Drain TMA copies that may still be in flight before the CTA exits.
+        for (int s = 0; s < TC_STAGES; ++s) mbar_wait(smem_u32(&bars[s]), 0, status, 0x8);
+    }
+    __syncthreads();
+    if (warp == 1) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(TC_TMEM_COLS)
+                     : "memory");
+    }
+}
+
+// The driver's tensor-map encoder, looked up at run time so that the library
+// loads (and its host-only entry points work) on machines without a driver.
+static PFN_cuTensorMapEncodeTiled_v12000 encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+static rgf_status encode_slices(CUtensorMap* map, const __nv_bfloat16* ptr, int Kp, long rows, long planes,
+                                int box_rows) {
+    cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)planes};
+    cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)rows * Kp * 2};
+    cuuint32_t box[3] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    PFN_cuTensorMapEncodeTiled_v12000 enc = encoder();
+    if (!enc) {
+        set_error("cuTensorMapEncodeTiled is not available from the driver");
+        return RGF_E_CUDA;
+    }
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)ptr, dims, strides, box, estr,
+                                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
+        return RGF_E_CUDA;
+    }
+    return RGF_OK;
+}
+
+rgf_status oz_gemm_tc(const OzGemm& g, cudaStream_t st) {
+    if (g.batch <= 0) return RGF_OK;
+    if (g.Kp % TC_BK != 0 || ((uintptr_t)g.As & 15) || ((uintptr_t)g.Bs & 15) || !g.status) {
+        set_error("oz_gemm_tc: bad slice layout");
+        return RGF_E_INVALID;
+    }
+    if (g.batch > 65535 || (long)g.batch * kSlices > 0x7fffffffL) {
+        set_error("oz_gemm_tc: batch too large");
+        return RGF_E_INVALID;
+    }
+    CUtensorMap ta, tb;
+    RGF_TRY(encode_slices(&ta, g.As, g.Kp, g.m, (long)g.batch * kSlices, TC_BM));
+    RGF_TRY(encode_slices(&tb, g.Bs, g.Kp, 2L * g.n, (long)g.batch * kSlices, TC_BN));
+    static bool attr = false;
+    if (!attr) {
+        RGF_CUDA_TRY(cudaFuncSetAttribute(k_oz_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+        attr = true;
+    }
+    dim3 grid(ceil_div(2L * g.n, TC_BN), ceil_div(g.m, TC_BM), g.batch);
+    // Only unmasked launches are timed: their work is exactly known.
+    const bool timed = gemm_timing_enabled() && g.active == nullptr;
+    cudaEvent_t ev = nullptr;
+    if (timed) gemm_timing_before(st, &ev);
+    k_oz_tc<<<grid, 128, TC_SMEM, st>>>(g, ta, tb);
+    RGF_LAUNCH_CHECK();
+    if (timed) {
+        // 21 slice-pair real products of M = m, N = 2n, K = 2k per batch entry.
+        const double pairs = (double)(kSlices * (kSlices + 1) / 2);
+        gemm_timing_after(st, ev, pairs * 2.0 * g.m * (2.0 * g.n) * (2.0 * g.k) * g.batch);
+    }
+    return RGF_OK;
+}
+
+}  // namespace rgf

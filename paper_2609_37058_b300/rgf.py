@@ -1,0 +1,316 @@
+"""ctypes binding of the C ABI in include/rgf.h (argument marshalling only).
+
+Every function below has the name of the C entry point it calls and does no
+arithmetic of its own: it turns numpy arrays (host memory) or torch tensors
+(device memory) into pointers and raises ``RGFError`` on a non-OK status.
+The compiled library ``librgf.so`` must exist next to this file; there is no
+fallback when it does not.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librgf.so")
+
+RGF_OK, RGF_E_INVALID, RGF_E_OOM, RGF_E_CUDA, RGF_E_NOT_READY, RGF_E_NOCONV, RGF_E_TIMEOUT, \
+    RGF_E_REJECTED, RGF_E_STATE = range(9)
+STATUS_NAMES = ["RGF_OK", "RGF_E_INVALID", "RGF_E_OOM", "RGF_E_CUDA", "RGF_E_NOT_READY",
+                "RGF_E_NOCONV", "RGF_E_TIMEOUT", "RGF_E_REJECTED", "RGF_E_STATE"]
+RGF_FP64, RGF_MIXED = 0, 1
+RGF_MEM_HOST, RGF_MEM_DEVICE = 0, 1
+RGF_LEAD_LEFT, RGF_LEAD_RIGHT = 0, 1
+RGF_FLAG_NOCONV_L, RGF_FLAG_NOCONV_R, RGF_FLAG_SINGULAR, RGF_FLAG_REFINE = 1, 2, 4, 8
+
+
+class RGFError(RuntimeError):
+    def __init__(self, status, where, message):
+        self.status = status
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__(f"{where}: {name}: {message}")
+
+
+class rgf_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("eta", ctypes.c_double), ("dec_tol", ctypes.c_double),
+                ("dec_max_iter", ctypes.c_int), ("ns_steps", ctypes.c_int),
+                ("energy_wave", ctypes.c_int)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+_D = ctypes.POINTER(ctypes.c_double)
+
+
+def lib():
+    """Load librgf.so (once).  Raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_2609_37058_b300.build`")
+    L = ctypes.CDLL(LIB_PATH)
+    sig = {
+        "rgf_options_default": (None, [ctypes.POINTER(rgf_options)]),
+        "rgf_plan_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.c_int,
+                                           ctypes.POINTER(rgf_options), _P]),
+        "rgf_set_device_blocks": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_int]),
+        "rgf_set_leads": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P, _P, _P, ctypes.c_int]),
+        "rgf_transmission": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, _P, _P, ctypes.c_int]),
+        "rgf_submit": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)]),
+        "rgf_poll": (ctypes.c_int, [ctypes.c_uint64, _P, _P, _P, ctypes.c_int]),
+        "rgf_plan_device_bytes": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_size_t)]),
+        "rgf_plan_energy_wave": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
+        "rgf_plan_destroy": (ctypes.c_int, [_P]),
+        "rgf_last_error": (ctypes.c_char_p, []),
+        "rgf_version": (ctypes.c_char_p, []),
+        "rgf_kernel_zgemm_f64": (ctypes.c_int, [ctypes.c_int] * 4 + [_P, _P, _P]),
+        "rgf_kernel_inverse_f64": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, _P]),
+        "rgf_kernel_inverse_c64": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, _P]),
+        "rgf_kernel_zgemm_mixed": (ctypes.c_int, [ctypes.c_int] * 4 + [_P, _P, _P, ctypes.c_int]),
+        "rgf_launch_count": (ctypes.c_ulonglong, []),
+        "rgf_plan_stats": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),
+        "rgf_gemm_timing": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                           ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(status, where):
+    if status != RGF_OK:
+        raise RGFError(status, where, rgf_last_error())
+
+
+def _ptr(x, dtype):
+    """(pointer, memspace) for a numpy array (host) or torch tensor (device)."""
+    if x is None:
+        return None, None
+    if isinstance(x, np.ndarray):
+        if x.dtype != dtype or not x.flags["C_CONTIGUOUS"]:
+            raise TypeError(f"expected a C-contiguous {np.dtype(dtype)} array")
+        return x.ctypes.data, RGF_MEM_HOST
+    import torch  # device memory comes from torch tensors
+    if not isinstance(x, torch.Tensor):
+        raise TypeError("expected numpy array or torch tensor")
+    tmap = {np.complex128: torch.complex128, np.float64: torch.float64, np.int32: torch.int32}
+    if x.dtype != tmap[dtype] or not x.is_contiguous():
+        raise TypeError(f"expected a contiguous {tmap[dtype]} tensor")
+    return x.data_ptr(), (RGF_MEM_DEVICE if x.is_cuda else RGF_MEM_HOST)
+
+
+def _mem_of(*ptrs):
+    spaces = {m for _, m in ptrs if m is not None}
+    if len(spaces) > 1:
+        raise TypeError("all arrays of one call must live in the same memory space")
+    return spaces.pop() if spaces else RGF_MEM_HOST
+
+
+# ----------------------------------------------------------------- C entry points
+def rgf_version() -> str:
+    return lib().rgf_version().decode()
+
+
+def rgf_last_error() -> str:
+    return lib().rgf_last_error().decode(errors="replace")
+
+
+def rgf_options_default() -> rgf_options:
+    o = rgf_options()
+    lib().rgf_options_default(ctypes.byref(o))
+    return o
+
+
+def rgf_plan_create(n_layers: int, b: int, opt: rgf_options | None = None, cuda_stream: int = 0):
+    h = _P()
+    s = lib().rgf_plan_create(ctypes.byref(h), int(n_layers), int(b),
+                              ctypes.byref(opt) if opt is not None else None,
+                              _P(cuda_stream) if cuda_stream else None)
+    _check(s, "rgf_plan_create")
+    return h
+
+
+def rgf_set_device_blocks(plan, H_diag, S_diag, H_lower, S_lower):
+    ps = [_ptr(a, np.complex128) for a in (H_diag, S_diag, H_lower, S_lower)]
+    mem = _mem_of(*ps)
+    _check(lib().rgf_set_device_blocks(plan, *[p for p, _ in ps], mem), "rgf_set_device_blocks")
+
+
+def rgf_set_leads(plan, side, H00, S00, H10, S10, Hc, Sc):
+    ps = [_ptr(a, np.complex128) for a in (H00, S00, H10, S10, Hc, Sc)]
+    mem = _mem_of(*ps)
+    _check(lib().rgf_set_leads(plan, int(side), *[p for p, _ in ps], mem), "rgf_set_leads")
+
+
+def rgf_transmission(plan, E, T, err=None, flags=None):
+    pe, pt = _ptr(E, np.float64), _ptr(T, np.float64)
+    pr, pf = _ptr(err, np.float64), _ptr(flags, np.int32)
+    mem = _mem_of(pe, pt, pr, pf)
+    n = int(E.shape[0])
+    _check(lib().rgf_transmission(plan, pe[0], n, pt[0], pr[0], pf[0], mem), "rgf_transmission")
+
+
+def rgf_submit(plan, E: np.ndarray) -> int:
+    pe = _ptr(E, np.float64)
+    if pe[1] != RGF_MEM_HOST:
+        raise TypeError("rgf_submit takes host energies")
+    t = ctypes.c_uint64()
+    _check(lib().rgf_submit(plan, pe[0], int(E.shape[0]), ctypes.byref(t)), "rgf_submit")
+    return t.value
+
+
+def rgf_poll(ticket: int, T, err=None, flags=None, timeout_us: int = -1) -> int:
+    """Returns the status (RGF_OK, RGF_E_NOT_READY, RGF_E_TIMEOUT); raises on errors."""
+    pt, pr, pf = _ptr(T, np.float64), _ptr(err, np.float64), _ptr(flags, np.int32)
+    s = lib().rgf_poll(ctypes.c_uint64(ticket), pt[0], pr[0], pf[0], int(timeout_us))
+    if s in (RGF_OK, RGF_E_NOT_READY, RGF_E_TIMEOUT):
+        return s
+    _check(s, "rgf_poll")
+    return s
+
+
+def rgf_plan_device_bytes(plan) -> int:
+    v = ctypes.c_size_t()
+    _check(lib().rgf_plan_device_bytes(plan, ctypes.byref(v)), "rgf_plan_device_bytes")
+    return v.value
+
+
+def rgf_plan_energy_wave(plan) -> int:
+    v = ctypes.c_int()
+    _check(lib().rgf_plan_energy_wave(plan, ctypes.byref(v)), "rgf_plan_energy_wave")
+    return v.value
+
+
+def rgf_plan_stats(plan):
+    """(waves, fp64_reseeds) counted since the plan was created."""
+    w, r = ctypes.c_longlong(), ctypes.c_longlong()
+    _check(lib().rgf_plan_stats(plan, ctypes.byref(w), ctypes.byref(r)), "rgf_plan_stats")
+    return w.value, r.value
+
+
+def rgf_plan_destroy(plan):
+    if plan:
+        _check(lib().rgf_plan_destroy(plan), "rgf_plan_destroy")
+
+
+# ----------------------------------------------------------------- kernel-level calls
+def _host(a, dtype):
+    if not isinstance(a, np.ndarray) or a.dtype != dtype or not a.flags["C_CONTIGUOUS"]:
+        raise TypeError(f"expected a C-contiguous {np.dtype(dtype)} host array")
+    return a.ctypes.data
+
+
+def rgf_kernel_zgemm_f64(A, B):
+    """C[i] = A[i] B[i] for complex128 arrays of shape (batch, m, k), (batch, k, n)."""
+    batch, m, k = A.shape
+    n = B.shape[2]
+    C = np.empty((batch, m, n), dtype=np.complex128)
+    _check(lib().rgf_kernel_zgemm_f64(batch, m, n, k, _host(A, np.complex128), _host(B, np.complex128),
+                                      C.ctypes.data), "rgf_kernel_zgemm_f64")
+    return C
+
+
+def rgf_kernel_zgemm_mixed(A, B, core=0):
+    batch, m, k = A.shape
+    n = B.shape[2]
+    C = np.empty((batch, m, n), dtype=np.complex128)
+    _check(lib().rgf_kernel_zgemm_mixed(batch, m, n, k, _host(A, np.complex128), _host(B, np.complex128),
+                                        C.ctypes.data, int(core)), "rgf_kernel_zgemm_mixed")
+    return C
+
+
+def rgf_kernel_inverse_f64(A):
+    """Inverse of each complex128 (b x b) matrix of A (batch, b, b); returns (inv, flags)."""
+    X = np.ascontiguousarray(A, dtype=np.complex128).copy()
+    flags = np.zeros(X.shape[0], dtype=np.int32)
+    _check(lib().rgf_kernel_inverse_f64(X.shape[0], X.shape[1], X.ctypes.data, flags.ctypes.data),
+           "rgf_kernel_inverse_f64")
+    return X, flags
+
+
+def rgf_kernel_inverse_c64(A):
+    X = np.ascontiguousarray(A, dtype=np.complex64).copy()
+    flags = np.zeros(X.shape[0], dtype=np.int32)
+    _check(lib().rgf_kernel_inverse_c64(X.shape[0], X.shape[1], X.ctypes.data, flags.ctypes.data),
+           "rgf_kernel_inverse_c64")
+    return X, flags
+
+
+def rgf_launch_count() -> int:
+    return int(lib().rgf_launch_count())
+
+
+def rgf_gemm_timing(enable: bool):
+    """Returns (total_ms, launches, flops) recorded since the last call and
+    sets recording on/off for what follows."""
+    ms, n, fl = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_double()
+    _check(lib().rgf_gemm_timing(int(bool(enable)), ctypes.byref(ms), ctypes.byref(n), ctypes.byref(fl)),
+           "rgf_gemm_timing")
+    return ms.value, n.value, fl.value
+
+
+# ----------------------------------------------------------------- convenience
+class Plan:
+    """Owns one rgf_plan_t.  ``precision`` is RGF_FP64 or RGF_MIXED."""
+
+    def __init__(self, n_layers, b, precision=RGF_FP64, eta=1e-6, energy_wave=0, ns_steps=4,
+                 dec_tol=1e-14, dec_max_iter=100, cuda_stream=0):
+        o = rgf_options_default()
+        o.precision, o.eta, o.energy_wave, o.ns_steps = precision, eta, energy_wave, ns_steps
+        o.dec_tol, o.dec_max_iter = dec_tol, dec_max_iter
+        self.n_layers, self.b = n_layers, b
+        self.handle = rgf_plan_create(n_layers, b, o, cuda_stream)
+
+    def set_device(self, dev):
+        """Copy a device description with H_diag/S_diag/H_lower/S_lower arrays
+        and lead_L/lead_R (H00, S00, H10, S10, Hc, Sc)."""
+        c = lambda a: np.ascontiguousarray(a, dtype=np.complex128)
+        N = dev.H_diag.shape[0]
+        low = (c(dev.H_lower), c(dev.S_lower)) if N > 1 else (None, None)
+        rgf_set_device_blocks(self.handle, c(dev.H_diag), c(dev.S_diag), *low)
+        for side, ld in ((RGF_LEAD_LEFT, dev.lead_L), (RGF_LEAD_RIGHT, dev.lead_R)):
+            rgf_set_leads(self.handle, side, c(ld.H00), c(ld.S00), c(ld.H10), c(ld.S10), c(ld.Hc),
+                          c(ld.Sc))
+
+    def transmission(self, E):
+        E = np.ascontiguousarray(E, dtype=np.float64)
+        T = np.empty_like(E)
+        err = np.empty_like(E)
+        flags = np.empty(E.shape[0], dtype=np.int32)
+        rgf_transmission(self.handle, E, T, err, flags)
+        return T, err, flags
+
+    @property
+    def stats(self):
+        return rgf_plan_stats(self.handle)
+
+    @property
+    def energy_wave(self):
+        return rgf_plan_energy_wave(self.handle)
+
+    @property
+    def device_bytes(self):
+        return rgf_plan_device_bytes(self.handle)
+
+    def close(self):
+        if self.handle:
+            rgf_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

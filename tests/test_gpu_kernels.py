@@ -1,0 +1,92 @@
+"""Single building blocks through the kernel-level C entry points, against
+numpy's FP64 linear algebra, at odd and tile-straddling sizes."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rgf():
+    from paper_2609_37058_b300 import build, rgf as r
+    build.build()
+    return r
+
+
+def crand(rng, *shape):
+    return (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)) / np.sqrt(2)
+
+
+SHAPES = [(1, 1, 1, 1), (2, 8, 8, 8), (3, 65, 33, 17), (2, 100, 70, 90), (2, 256, 256, 256),
+          (1, 320, 320, 320), (2, 128, 200, 64)]
+
+
+@pytest.mark.parametrize("batch,m,n,k", SHAPES)
+def test_zgemm_f64(rgf, batch, m, n, k):
+    rng = np.random.default_rng(m * 7 + n)
+    A, B = crand(rng, batch, m, k), crand(rng, batch, k, n)
+    C = rgf.rgf_kernel_zgemm_f64(A, B)
+    ref = A @ B
+    assert np.abs(C - ref).max() <= 1e-13 * np.sqrt(k) * np.abs(ref).max() + 1e-300
+
+
+def mixed_bound(A, B):
+    """Per-entry bound of the slice-product error: the 6 x 8-bit slices keep
+    47 bits of each entry relative to its row (A) or column (B) maximum, so
+    each of the k terms is off by at most ~2^-45 rowmax * colmax."""
+    k = A.shape[2]
+    ra = np.maximum(np.abs(A.real), np.abs(A.imag)).max(axis=2)[:, :, None]
+    cb = np.maximum(np.abs(B.real), np.abs(B.imag)).max(axis=1)[:, None, :]
+    return 4.0 * k * 2.0 ** -45 * ra * cb
+
+
+@pytest.mark.parametrize("core", [0, 1], ids=["tc", "mma"])
+@pytest.mark.parametrize("batch,m,n,k", SHAPES)
+def test_zgemm_mixed(rgf, core, batch, m, n, k):
+    rng = np.random.default_rng(m + 3 * k)
+    A, B = crand(rng, batch, m, k), crand(rng, batch, k, n)
+    # Rows and columns of very different size exercise the per-row/per-column scales.
+    A[:, ::3, :] *= 1e-5
+    B[:, :, ::4] *= 1e4
+    C = rgf.rgf_kernel_zgemm_mixed(A, B, core=core)
+    ref = A @ B
+    bound = mixed_bound(A, B)
+    err = np.abs(C - ref)
+    assert np.all(err <= bound), (err / bound).max()
+
+
+def test_mixed_cores_agree(rgf):
+    rng = np.random.default_rng(5)
+    A, B = crand(rng, 3, 256, 256), crand(rng, 3, 256, 256)
+    C0 = rgf.rgf_kernel_zgemm_mixed(A, B, core=0)
+    C1 = rgf.rgf_kernel_zgemm_mixed(A, B, core=1)
+    assert np.all(np.abs(C0 - C1) <= mixed_bound(A, B))
+
+
+@pytest.mark.parametrize("b", [1, 2, 8, 31, 33, 96, 100, 256, 320])
+def test_inverse_f64(rgf, b):
+    rng = np.random.default_rng(b)
+    A = crand(rng, 3, b, b) + 2.0 * np.eye(b)
+    if b > 1:
+        A[1, 0, 0] = 0.0  # forces a row interchange
+    X, flags = rgf.rgf_kernel_inverse_f64(A)
+    ref = np.linalg.inv(A)
+    assert np.all(flags == 0)
+    assert np.linalg.norm(X - ref) <= 1e-11 * np.linalg.norm(ref)
+
+
+def test_inverse_flags_singular(rgf):
+    A = np.zeros((2, 4, 4), dtype=np.complex128)
+    A[1] = np.eye(4)
+    X, flags = rgf.rgf_kernel_inverse_f64(A)
+    assert flags[0] & rgf.RGF_FLAG_SINGULAR and flags[1] == 0
+    assert np.allclose(X[1], np.eye(4))
+
+
+@pytest.mark.parametrize("b", [8, 96, 256])
+def test_inverse_c64(rgf, b):
+    rng = np.random.default_rng(b + 1)
+    A = (crand(rng, 2, b, b) + 2.0 * np.eye(b)).astype(np.complex64)
+    X, flags = rgf.rgf_kernel_inverse_c64(A)
+    r = np.abs(X.astype(np.complex128) @ A.astype(np.complex128) - np.eye(b)).max()
+    assert np.all(flags == 0) and r < 1e-4
