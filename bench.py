@@ -188,6 +188,8 @@ def main():
     plan.set_device(dev)
     E_d = torch.tensor(E_all, dtype=torch.float64, device="cuda")
     T_d = torch.zeros(n_E, dtype=torch.float64, device="cuda")
+    err_d = torch.zeros(n_E, dtype=torch.float64, device="cuda")
+    flags_d = torch.zeros(n_E, dtype=torch.int32, device="cuda")
 
     def wave(k):
         start = ((k * world + rank) * W) % n_E
@@ -195,7 +197,7 @@ def main():
 
     def step(k):
         s, c = wave(k)
-        rgf.rgf_transmission(plan.handle, E_d[s:s + c], T_d[s:s + c])
+        rgf.rgf_transmission(plan.handle, E_d[s:s + c], T_d[s:s + c], err_d[s:s + c], flags_d[s:s + c])
         return c
 
     for k in range(args.warmup):
@@ -244,6 +246,13 @@ def main():
         done_all = float(done)
     value = done_all / elapsed
     T_timed = T_d.cpu().numpy()
+    fl = flags_d.cpu().numpy()
+    ts, tc_ = wave(args.warmup)
+    fl_t = fl[ts:ts + tc_]
+    flag_counts = {"refine": int(np.sum((fl_t & rgf.RGF_FLAG_REFINE) != 0)),
+                   "singular": int(np.sum((fl_t & rgf.RGF_FLAG_SINGULAR) != 0)),
+                   "noconv": int(np.sum((fl_t & (rgf.RGF_FLAG_NOCONV_L | rgf.RGF_FLAG_NOCONV_R)) != 0)),
+                   "max_err_estimate": float(err_d.cpu().numpy()[ts:ts + tc_].max())}
 
     if rank != 0:
         plan.close()
@@ -265,7 +274,7 @@ def main():
     h2d = dev.nbytes() + sum(getattr(l, f).nbytes for l in (dev.lead_L, dev.lead_R)
                              for f in ("H00", "S00", "H10", "S10", "Hc", "Sc")) + E_h.nbytes
     d2h = T_h.nbytes + err_h.nbytes + fl_h.nbytes
-    waves_done, reseeds = plan.stats
+    waves_done, reseeds, dec_redo = plan.stats
     plan.close()
 
     # ---------------------------------------------------------- FP64 GPU path
@@ -323,6 +332,8 @@ def main():
         "parity_sample": {"energies": nb, "max_abs_dT": float(dT.max()), "bar": 1e-6},
         "fp64_gpu": fp64,
         "fp64_reseeds": reseeds,
+        "fp64_decimation_redo": dec_redo,
+        "flags_first_timed_wave": flag_counts,
         "clocks": clk,
     }
     print(json.dumps(line), flush=True)

@@ -84,11 +84,10 @@ typedef enum { RGF_LEAD_LEFT = 0, RGF_LEAD_RIGHT = 1 } rgf_side;
 #define RGF_FLAG_NOCONV_L   0x1  /* left-lead decimation hit dec_max_iter  */
 #define RGF_FLAG_NOCONV_R   0x2  /* right-lead decimation hit dec_max_iter */
 #define RGF_FLAG_SINGULAR   0x4  /* an exactly zero pivot in an inverse     */
-#define RGF_FLAG_REFINE     0x8  /* mixed path: an FP32 inverse seed did not
-                                    contract (||I - M X||_F >= 0.5) and was
-                                    replaced by an FP64 seed, or the last
-                                    Newton-Schulz step left ||I - M X||_F
-                                    above 3e-7                               */
+#define RGF_FLAG_REFINE     0x8  /* mixed path: an FP32 inverse seed had
+                                    ||I - M X||_F >= 0.5 and was replaced by
+                                    an FP64 seed, or the last Newton-Schulz
+                                    step left ||I - M X||_F above 3e-7      */
 
 typedef struct {
     int precision;     /* rgf_precision; default RGF_FP64 */
@@ -98,7 +97,7 @@ typedef struct {
     int dec_max_iter;  /* default 100 */
     int ns_steps;      /* most Newton-Schulz steps per mixed inverse; each
                           matrix stops once its residual predicts
-                          convergence (usually after 2); default 4 */
+                          convergence (usually after 2); default 6 */
     int energy_wave;   /* energies per device pass; 0 = chosen from b and
                           free memory */
 } rgf_options;
@@ -147,9 +146,12 @@ rgf_status rgf_submit(rgf_plan_t plan, const double* E, int n_E, rgf_ticket_t* t
  * released by the first call that returns RGF_OK. */
 rgf_status rgf_poll(rgf_ticket_t ticket, double* T, double* err, int* flags, int timeout_us);
 
-/* Counters of a plan since its creation: waves run and mixed-path inverses
- * whose FP32 seed was replaced by an FP64 seed (either may be NULL). */
-rgf_status rgf_plan_stats(rgf_plan_t plan, long long* waves, long long* fp64_reseeds);
+/* Counters of a plan since its creation (each output may be NULL): waves
+ * run; mixed-path inverses whose FP32 seed was replaced by an FP64 seed; and
+ * mixed-path lead decimations redone in FP64 because the double-float
+ * recursion inverted matrices with condition estimate above 1e6 (or did not
+ * converge). */
+rgf_status rgf_plan_stats(rgf_plan_t plan, long long* waves, long long* fp64_reseeds, long long* dec_fp64_redo);
 
 /* Device bytes the plan holds (blocks + workspace for one energy wave). */
 rgf_status rgf_plan_device_bytes(rgf_plan_t plan, size_t* bytes);

@@ -100,7 +100,7 @@ void rgf_options_default(rgf_options* opt) {
     opt->eta = 1e-6;
     opt->dec_tol = 1e-14;
     opt->dec_max_iter = 100;
-    opt->ns_steps = 4;
+    opt->ns_steps = 6;
     opt->energy_wave = 0;
 }
 
@@ -242,10 +242,11 @@ rgf_status rgf_plan_device_bytes(rgf_plan_t p, size_t* bytes) {
     return RGF_OK;
 }
 
-rgf_status rgf_plan_stats(rgf_plan_t p, long long* waves, long long* fp64_reseeds) {
+rgf_status rgf_plan_stats(rgf_plan_t p, long long* waves, long long* fp64_reseeds, long long* dec_fp64_redo) {
     RGF_TRY(check_plan(p));
     if (waves) *waves = p->n_waves;
     if (fp64_reseeds) *fp64_reseeds = p->n_reseeds;
+    if (dec_fp64_redo) *dec_fp64_redo = p->n_dec_redo;
     return RGF_OK;
 }
 

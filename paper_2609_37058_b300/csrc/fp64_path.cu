@@ -41,6 +41,72 @@ inline ZGemm gemm_sq(int batch, int b, double2 alpha, const double2* A, const do
 }
 }  // namespace
 
+// Sancho-Rubio decimation of both leads in FP64 for batch entries s*W + e
+// (s = 0 left, 1 right) whose mask entry is nonzero (mask may be null: all).
+// pool must hold kDecMats*2W matrices, inv_ws inv_f64_workspace_bytes(2W, b).
+// On return *g_out points at the 2W surface Green's functions inside pool
+// (entries outside the mask untouched), p->d_dec_flags gathers SINGULAR bits
+// and dec_active[i] != 0 marks entries that hit dec_max_iter.
+rgf_status fp64_decimate(rgf_plan_s* p, int W, const int* mask, double2* pool_base, void* inv_ws,
+                         int* dec_active, double2** g_out) {
+    cudaStream_t st = p->stream;
+    const int b = p->b;
+    const long nn = (long)b * b;
+    const double eta = p->opt.eta;
+    const double2 one = make_double2(1.0, 0.0), mone = make_double2(-1.0, 0.0);
+    Pool pool{pool_base, nn, W};
+    const double* E = p->d_E;
+    double2 *eps_s = pool.at(0), *eps = pool.at(2), *alpha = pool.at(4), *beta = pool.at(6);
+    double2 *g = pool.at(8), *ga = pool.at(10), *gb = pool.at(12);
+    double2 *t1 = pool.at(14), *t2 = pool.at(16), *t3 = pool.at(18), *t4 = pool.at(20);
+    const int W2 = 2 * W;
+    double2** L = p->lead[0];
+    double2** R = p->lead[1];
+    {
+        FormSrc a{{L[1], R[1]}, {L[0], R[0]}, {0, 0}};
+        RGF_TRY(form_f64(W, 2, b, E, eta, a, eps, nullptr, 0.0, mask, st));
+        RGF_TRY(copy_f64(W2, b, eps_s, eps, mask, st));
+        // Outward coupling: left lead M_{j,j-1} (lower), right lead M_{j,j+1} (upper).
+        FormSrc al{{L[3], R[3]}, {L[2], R[2]}, {0, 1}};
+        FormSrc be{{L[3], R[3]}, {L[2], R[2]}, {1, 0}};
+        RGF_TRY(form_f64(W, 2, b, E, eta, al, alpha, nullptr, 0.0, mask, st));
+        RGF_TRY(form_f64(W, 2, b, E, eta, be, beta, nullptr, 0.0, mask, st));
+        RGF_TRY(fro_norm_f64(W2, b, eps, p->d_anorm, st));
+    }
+    int* act = dec_active;
+    if (mask) {
+        RGF_CUDA_TRY(cudaMemcpyAsync(act, mask, sizeof(int) * W2, cudaMemcpyDeviceToDevice, st));
+    } else {
+        std::vector<int> ones(W2, 1);
+        RGF_CUDA_TRY(cudaMemcpyAsync(act, ones.data(), sizeof(int) * W2, cudaMemcpyHostToDevice, st));
+    }
+    RGF_CUDA_TRY(cudaMemsetAsync(p->d_iters, 0, sizeof(int) * W2, st));
+    for (int it = 1; it <= p->opt.dec_max_iter; ++it) {
+        RGF_TRY(copy_f64(W2, b, g, eps, act, st));
+        RGF_TRY(inv_f64(W2, b, g, nn, inv_ws, p->d_dec_flags, act, st));
+        RGF_TRY(zgemm_f64(gemm_sq(W2, b, one, g, alpha, ga, act), st));
+        RGF_TRY(zgemm_f64(gemm_sq(W2, b, one, g, beta, gb, act), st));
+        RGF_TRY(zgemm_f64(gemm_sq(W2, b, one, alpha, gb, t1, act), st));   // alpha g beta
+        RGF_TRY(zgemm_f64(gemm_sq(W2, b, one, beta, ga, t2, act), st));    // beta g alpha
+        RGF_TRY(zgemm_f64(gemm_sq(W2, b, mone, alpha, ga, t3, act), st));  // -alpha g alpha
+        RGF_TRY(zgemm_f64(gemm_sq(W2, b, mone, beta, gb, t4, act), st));   // -beta g beta
+        RGF_TRY(dec_update_f64(W2, b, eps_s, eps, t1, t2, act, st));
+        std::swap(alpha, t3);
+        std::swap(beta, t4);
+        RGF_CUDA_TRY(cudaMemsetAsync(p->d_remaining, 0, sizeof(int), st));
+        RGF_TRY(dec_check_f64(W2, b, alpha, beta, p->d_anorm, p->opt.dec_tol, it, act, p->d_iters,
+                              p->d_remaining, st));
+        RGF_CUDA_TRY(cudaMemcpyAsync(p->h_remaining, p->d_remaining, sizeof(int), cudaMemcpyDeviceToHost, st));
+        RGF_CUDA_TRY(cudaStreamSynchronize(st));
+        if (*p->h_remaining == 0) break;
+    }
+    // g_s = eps_s^-1
+    RGF_TRY(copy_f64(W2, b, g, eps_s, mask, st));
+    RGF_TRY(inv_f64(W2, b, g, nn, inv_ws, nullptr, mask, st));
+    *g_out = g;
+    return RGF_OK;
+}
+
 size_t fp64_workspace_bytes(int W, int b) {
     const size_t nn = (size_t)b * b;
     return (size_t)kPoolMats * W * nn * sizeof(double2) + inv_f64_workspace_bytes(2 * W, b) + 1024;
@@ -61,53 +127,13 @@ rgf_status fp64_wave(rgf_plan_s* p, int W) {
     RGF_CUDA_TRY(cudaMemsetAsync(p->d_err, 0, sizeof(double) * W, st));
 
     // ---------------------------------------------------------- decimation
-    // Batch entry s*W + e: s = 0 left lead, s = 1 right lead.
-    double2 *eps_s = pool.at(0), *eps = pool.at(2), *alpha = pool.at(4), *beta = pool.at(6);
-    double2 *g = pool.at(8), *ga = pool.at(10), *gb = pool.at(12);
-    double2 *t1 = pool.at(14), *t2 = pool.at(16), *t3 = pool.at(18), *t4 = pool.at(20);
+    double2* g = nullptr;
+    RGF_TRY(fp64_decimate(p, W, nullptr, pool.at(0), inv_ws, p->d_active, &g));
+    RGF_TRY(merge_dec_flags(W, p->d_dec_flags, p->d_active, p->d_flags, st));
     const int W2 = 2 * W;
+    double2 *t1 = pool.at(14), *t2 = pool.at(16), *t3 = pool.at(18);
     double2** L = p->lead[0];
     double2** R = p->lead[1];
-    {
-        FormSrc a{{L[1], R[1]}, {L[0], R[0]}, {0, 0}};
-        RGF_TRY(form_f64(W, 2, b, E, eta, a, eps, nullptr, 0.0, nullptr, st));
-        RGF_TRY(copy_f64(W2, b, eps_s, eps, nullptr, st));
-        // Outward coupling: left lead M_{j,j-1} (lower), right lead M_{j,j+1} (upper).
-        FormSrc al{{L[3], R[3]}, {L[2], R[2]}, {0, 1}};
-        FormSrc be{{L[3], R[3]}, {L[2], R[2]}, {1, 0}};
-        RGF_TRY(form_f64(W, 2, b, E, eta, al, alpha, nullptr, 0.0, nullptr, st));
-        RGF_TRY(form_f64(W, 2, b, E, eta, be, beta, nullptr, 0.0, nullptr, st));
-        RGF_TRY(fro_norm_f64(W2, b, eps, p->d_anorm, st));
-    }
-    {
-        std::vector<int> ones(W2, 1);
-        RGF_CUDA_TRY(cudaMemcpyAsync(p->d_active, ones.data(), sizeof(int) * W2, cudaMemcpyHostToDevice, st));
-        RGF_CUDA_TRY(cudaMemsetAsync(p->d_iters, 0, sizeof(int) * W2, st));
-        int* act = p->d_active;
-        for (int it = 1; it <= p->opt.dec_max_iter; ++it) {
-            RGF_TRY(copy_f64(W2, b, g, eps, act, st));
-            RGF_TRY(inv_f64(W2, b, g, nn, inv_ws, p->d_dec_flags, act, st));
-            RGF_TRY(zgemm_f64(gemm_sq(W2, b, one, g, alpha, ga, act), st));
-            RGF_TRY(zgemm_f64(gemm_sq(W2, b, one, g, beta, gb, act), st));
-            RGF_TRY(zgemm_f64(gemm_sq(W2, b, one, alpha, gb, t1, act), st));   // alpha g beta
-            RGF_TRY(zgemm_f64(gemm_sq(W2, b, one, beta, ga, t2, act), st));    // beta g alpha
-            RGF_TRY(zgemm_f64(gemm_sq(W2, b, mone, alpha, ga, t3, act), st));  // -alpha g alpha
-            RGF_TRY(zgemm_f64(gemm_sq(W2, b, mone, beta, gb, t4, act), st));   // -beta g beta
-            RGF_TRY(dec_update_f64(W2, b, eps_s, eps, t1, t2, act, st));
-            std::swap(alpha, t3);
-            std::swap(beta, t4);
-            RGF_CUDA_TRY(cudaMemsetAsync(p->d_remaining, 0, sizeof(int), st));
-            RGF_TRY(dec_check_f64(W2, b, alpha, beta, p->d_anorm, p->opt.dec_tol, it, act, p->d_iters,
-                                  p->d_remaining, st));
-            RGF_CUDA_TRY(cudaMemcpyAsync(p->h_remaining, p->d_remaining, sizeof(int), cudaMemcpyDeviceToHost, st));
-            RGF_CUDA_TRY(cudaStreamSynchronize(st));
-            if (*p->h_remaining == 0) break;
-        }
-        RGF_TRY(merge_dec_flags(W, p->d_dec_flags, p->d_active, p->d_flags, st));
-        // g_s = eps_s^-1
-        RGF_TRY(copy_f64(W2, b, g, eps_s, nullptr, st));
-        RGF_TRY(inv_f64(W2, b, g, nn, inv_ws, nullptr, nullptr, st));
-    }
 
     // ---------------------------------------------------------- self-energies
     // Sigma_L = Lc_L g_L Uc_L, Sigma_R = Uc_R g_R Lc_R with Lc = z Sc - Hc

@@ -117,6 +117,7 @@ static inline int gj_nb(int b) { return b <= 320 ? (b < 32 ? b : 32) : 16; }
 
 template <typename T2>
 size_t inv_workspace_bytes_t(int batch, int b) {
+    // Pbar (b x nb) and T (nb x b) per matrix, plus pivots.
     const int nb = gj_nb(b);
     return (size_t)batch * ((size_t)b * nb * sizeof(T2) * 2 + (size_t)b * sizeof(int)) + 256;
 }
@@ -129,34 +130,37 @@ __device__ __forceinline__ void argmax_merge(R& v, int& i, R v2, int i2) {
     }
 }
 
-template <typename T2>
+// Panel kernel: 256 threads; lane = panel column (NB <= 32), warp w owns rows
+// w, w + 8, ...  The panel lives in shared memory with a row pitch of NB + 1
+// elements so that column reads are (almost) free of bank conflicts.
+template <typename T2, int NB>
 __global__ void __launch_bounds__(256) k_gj_panel(int b, int k0, int nbk, T2* A, long sA, T2* Pbar, int* piv,
                                                   int* flags, const int* active) {
     using C = CT<T2>;
     using R = typename C::R;
+    constexpr int P = NB + 1;
     const int bi = blockIdx.x;
     if (active && !active[bi]) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T2* pan = reinterpret_cast<T2*>(smem_raw);  // b x nbk
-    T2* fcol = pan + (long)b * nbk;              // b
+    T2* pan = reinterpret_cast<T2*>(smem_raw);  // b x P
+    T2* fcol = pan + (long)b * P;                // b
     __shared__ R red_v[8];
     __shared__ int red_i[8];
     __shared__ int s_piv;
     T2* Ab = A + (long)bi * sA;
     int* pv = piv + (long)bi * b;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const bool col_ok = lane < nbk;
 
-    for (int i = tid; i < b * nbk; i += blockDim.x) {
-        const int r = i / nbk, c = i % nbk;
-        pan[i] = Ab[(long)r * b + k0 + c];
-    }
+    for (int r = wid; r < b; r += 8)
+        if (col_ok) pan[r * P + lane] = Ab[(long)r * b + k0 + lane];
     __syncthreads();
 
     for (int jj = 0; jj < nbk; ++jj) {
         const int j = k0 + jj;
         R bv = -1;
         int bidx = b;
-        for (int r = j + tid; r < b; r += blockDim.x) argmax_merge<R>(bv, bidx, cabs2(pan[r * nbk + jj]), r);
+        for (int r = j + tid; r < b; r += 256) argmax_merge<R>(bv, bidx, cabs2(pan[r * P + jj]), r);
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
             R ov = __shfl_down_sync(0xffffffffu, bv, off);
@@ -171,7 +175,7 @@ __global__ void __launch_bounds__(256) k_gj_panel(int b, int k0, int nbk, T2* A,
         if (tid == 0) {
             R v = red_v[0];
             int ix = red_i[0];
-            for (int w = 1; w < (int)(blockDim.x >> 5); ++w) argmax_merge<R>(v, ix, red_v[w], red_i[w]);
+            for (int w = 1; w < 8; ++w) argmax_merge<R>(v, ix, red_v[w], red_i[w]);
             if (ix >= b) ix = j;
             s_piv = ix;
             pv[j] = ix;
@@ -179,43 +183,42 @@ __global__ void __launch_bounds__(256) k_gj_panel(int b, int k0, int nbk, T2* A,
         }
         __syncthreads();
         const int p = s_piv;
-        if (p != j) {
-            for (int c = tid; c < nbk; c += blockDim.x) {
-                T2 t = pan[j * nbk + c];
-                pan[j * nbk + c] = pan[p * nbk + c];
-                pan[p * nbk + c] = t;
-            }
+        if (p != j && tid < nbk) {
+            T2 t = pan[j * P + tid];
+            pan[j * P + tid] = pan[p * P + tid];
+            pan[p * P + tid] = t;
         }
         __syncthreads();
-        const T2 inv_d = cinv(pan[j * nbk + jj]);
-        for (int r = tid; r < b; r += blockDim.x) fcol[r] = pan[r * nbk + jj];
+        const T2 inv_d = cinv(pan[j * P + jj]);
+        for (int r = tid; r < b; r += 256) fcol[r] = pan[r * P + jj];
         __syncthreads();
-        for (int c = tid; c < nbk; c += blockDim.x)
-            pan[j * nbk + c] = (c == jj) ? inv_d : cmul(pan[j * nbk + c], inv_d);
+        if (tid < nbk) pan[j * P + tid] = (tid == jj) ? inv_d : cmul(pan[j * P + tid], inv_d);
         __syncthreads();
-        for (int i = tid; i < b * nbk; i += blockDim.x) {
-            const int r = i / nbk, c = i % nbk;
-            if (r == j) continue;
-            const T2 f = fcol[r];
-            if (c == jj) {
-                pan[i] = cmul(C::make(-f.x, -f.y), inv_d);
-            } else {
-                T2 v = pan[i];
-                const T2 pj = pan[j * nbk + c];
-                v.x -= f.x * pj.x - f.y * pj.y;
-                v.y -= f.x * pj.y + f.y * pj.x;
-                pan[i] = v;
+        if (col_ok) {
+            const T2 pj = pan[j * P + lane];
+            for (int r = wid; r < b; r += 8) {
+                if (r == j) continue;
+                const T2 f = fcol[r];
+                if (lane == jj) {
+                    pan[r * P + lane] = cmul(C::make(-f.x, -f.y), inv_d);
+                } else {
+                    T2 v = pan[r * P + lane];
+                    v.x -= f.x * pj.x - f.y * pj.y;
+                    v.y -= f.x * pj.y + f.y * pj.x;
+                    pan[r * P + lane] = v;
+                }
             }
         }
         __syncthreads();
     }
     T2* Pb = Pbar + (long)bi * b * nbk;
-    for (int i = tid; i < b * nbk; i += blockDim.x) {
-        const int r = i / nbk, c = i % nbk;
-        T2 v = pan[i];
-        Ab[(long)r * b + k0 + c] = v;
-        if (r == k0 + c) v.x -= 1;
-        Pb[i] = v;
+    if (col_ok) {
+        for (int r = wid; r < b; r += 8) {
+            T2 v = pan[r * P + lane];
+            Ab[(long)r * b + k0 + lane] = v;
+            if (r == k0 + lane) v.x -= 1;
+            Pb[(long)r * nbk + lane] = v;
+        }
     }
 }
 
@@ -243,21 +246,35 @@ __global__ void k_gj_swap(int b, int k0, int nbk, T2* A, long sA, const int* piv
     for (int jj = 0; jj < nbk; ++jj) Tb[(long)jj * b + c] = Ab[(long)(k0 + jj) * b + c];
 }
 
+// Undo the column interchanges: column c of the result is stored column
+// src[c], where src is the identity with the swaps (j, piv[j]) applied for
+// j = b-1 down to 0.  One CTA per (32-row block, matrix); rows go through
+// shared memory so that reads and writes are coalesced.
 template <typename T2>
-__global__ void k_gj_unpermute(int b, T2* A, long sA, const int* piv, const int* active) {
+__global__ void __launch_bounds__(256) k_gj_unpermute(int b, T2* A, long sA, const int* piv, const int* active) {
     const int bi = blockIdx.y;
     if (active && !active[bi]) return;
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= b) return;
-    T2* row = A + (long)bi * sA + (long)r * b;
+    extern __shared__ __align__(16) unsigned char smem_up[];
+    int* src = reinterpret_cast<int*>(smem_up);
+    T2* row = reinterpret_cast<T2*>(smem_up + ((b * sizeof(int) + 15) & ~size_t(15)));
     const int* pv = piv + (long)bi * b;
-    for (int j = b - 1; j >= 0; --j) {
-        const int p = pv[j];
-        if (p != j) {
-            T2 t = row[j];
-            row[j] = row[p];
-            row[p] = t;
+    if (threadIdx.x == 0) {
+        for (int c = 0; c < b; ++c) src[c] = c;
+        for (int j = b - 1; j >= 0; --j) {
+            const int p = pv[j];
+            const int t = src[j];
+            src[j] = src[p];
+            src[p] = t;
         }
+    }
+    __syncthreads();
+    T2* Ab = A + (long)bi * sA;
+    const int r1 = min(b, (int)(blockIdx.x + 1) * 32);
+    for (int r = blockIdx.x * 32; r < r1; ++r) {
+        for (int c = threadIdx.x; c < b; c += blockDim.x) row[c] = Ab[(long)r * b + c];
+        __syncthreads();
+        for (int c = threadIdx.x; c < b; c += blockDim.x) Ab[(long)r * b + c] = row[src[c]];
+        __syncthreads();
     }
 }
 
@@ -268,17 +285,23 @@ rgf_status inv_t(int batch, int b, T2* A, long sA, void* ws, int* flags, const i
     T2* Pbar = (T2*)ws;
     T2* T = Pbar + (size_t)batch * b * nb;
     int* piv = (int*)(T + (size_t)batch * b * nb);
-    const size_t smem = ((size_t)b * nb + b) * sizeof(T2);
+    const size_t smem = ((size_t)b * (nb + 1) + b) * sizeof(T2);
     if (smem > 200 * 1024) {
         set_error("inverse: b = %d needs %zu bytes of shared memory", b, smem);
         return RGF_E_INVALID;
     }
-    if (smem > 48 * 1024)
-        RGF_CUDA_TRY(cudaFuncSetAttribute(k_gj_panel<T2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    auto panel = (nb == 32) ? k_gj_panel<T2, 32> : k_gj_panel<T2, 16>;
+    if (nb != 32 && nb != 16 && b >= 32) {
+        set_error("inverse: unsupported panel width %d", nb);
+        return RGF_E_INVALID;
+    }
+    if (b < 32) panel = k_gj_panel<T2, 32>;  // nb = b < 32 columns of a 32-lane panel
+    if (smem > 48 * 1024) RGF_CUDA_TRY(cudaFuncSetAttribute(panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int pitch_nb = (panel == k_gj_panel<T2, 16>) ? 16 : 32;
     for (int k0 = 0; k0 < b; k0 += nb) {
         const int nbk = (b - k0) < nb ? (b - k0) : nb;
-        const size_t sm = ((size_t)b * nbk + b) * sizeof(T2);
-        k_gj_panel<T2><<<batch, 256, sm, st>>>(b, k0, nbk, A, sA, Pbar, piv, flags, active);
+        const size_t sm = ((size_t)b * (pitch_nb + 1) + b) * sizeof(T2);
+        panel<<<batch, 256, sm, st>>>(b, k0, nbk, A, sA, Pbar, piv, flags, active);
         RGF_LAUNCH_CHECK();
         if (nbk < b) {
             dim3 g2(ceil_div(b, 128), batch);
@@ -309,8 +332,9 @@ rgf_status inv_t(int batch, int b, T2* A, long sA, void* ws, int* flags, const i
             RGF_TRY(zgemm_t<T2>(g, st));
         }
     }
-    dim3 g3(ceil_div(b, 128), batch);
-    k_gj_unpermute<T2><<<g3, 128, 0, st>>>(b, A, sA, piv, active);
+    dim3 g3(ceil_div(b, 32), batch);
+    const size_t smu = ((b * sizeof(int) + 15) & ~size_t(15)) + (size_t)b * sizeof(T2);
+    k_gj_unpermute<T2><<<g3, 256, smu, st>>>(b, A, sA, piv, active);
     RGF_LAUNCH_CHECK();
     return RGF_OK;
 }

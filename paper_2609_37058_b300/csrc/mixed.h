@@ -88,20 +88,31 @@ rgf_status gamma_dfc(int batch, int b, const float4* sigma, float4* gamma, cudaS
 rgf_status axpy_dfc(int batch, int b, float alpha, const float4* X, float4* Y, cudaStream_t st);
 // Newton-Schulz bookkeeping for step s of at most max_steps on batch
 // entries i (energy e = i mod W), given R = I - M X:
-//   err[e] = max(err[e], |R_i|_F);
-//   on step 0, entries with |R_i|_F >= 0.5 (or not finite) get bad[i] = 1,
-//     are counted in *bad_count and flagged RGF_FLAG_REFINE (their FP32
-//     seed does not contract; the caller reseeds them in FP64);
+//   step 0: entries with |R_i|_F >= 0.5 (or not finite) get bad[i] = 1,
+//     are counted in *bad_count and flagged RGF_FLAG_REFINE; the caller
+//     reseeds them with an FP64 inverse;
 //   next_act[i] = act[i] && |R_i|_F > 3e-7 (after this step's correction
 //     the residual is below |R_i|^2 <= 1e-13, so the entry is done);
-//   on the last step an entry still above 3e-7 is flagged RGF_FLAG_REFINE.
+//   err[e] = max(err[e], estimated final residual); an entry still above
+//     3e-7 on the last step is flagged RGF_FLAG_REFINE.
 rgf_status ns_check(int batch, int W, int b, const float4* R, double* err, int* flags, int step, int max_steps,
                     const int* act, int* next_act, int* bad, int* bad_count, cudaStream_t st);
+// Masked conversions between df and FP64 complex (entries with mask[i]).
+rgf_status dfc_to_c128(int batch, int b, const float4* X, double2* Y, const int* mask, cudaStream_t st);
+rgf_status c128_to_dfc(int batch, int b, const double2* X, float4* Y, const int* mask, cudaStream_t st);
 // out[i] = act ? act[i] : 1
 rgf_status mask_init(int batch, const int* act, int* out, cudaStream_t st);
 // Masked conversions between df and FP64 complex (entries with mask[i]).
 rgf_status dfc_to_c128(int batch, int b, const float4* X, double2* Y, const int* mask, cudaStream_t st);
 rgf_status c128_to_dfc(int batch, int b, const double2* X, float4* Y, const int* mask, cudaStream_t st);
+// Decimation conditioning: kmax[i] = max(kmax[i], |g_i|_F |eps_i|_F).
+rgf_status dec_kmax(int batch, int b, const float4* g, const float4* eps, double* kmax, const int* act,
+                    cudaStream_t st);
+// redo[i] = (kmax[i] > thr, or not finite, or still_active[i]); counted.
+rgf_status dec_redo_mask(int batch, const double* kmax, double thr, const int* still_active, int* redo, int* count,
+                         cudaStream_t st);
+// out[i] = sel[i] ? a[i] : b[i]
+rgf_status select_int(int batch, const int* sel, const int* a, const int* b, int* out, cudaStream_t st);
 // T[i] = Re sum X_jk conj(Y_jk) reduced in FP64 from df inputs.
 rgf_status trace_dfc(int batch, int b, const float4* X, const float4* Y, double* T, double* Ti, cudaStream_t st);
 

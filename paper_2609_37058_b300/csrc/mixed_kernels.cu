@@ -563,10 +563,13 @@ __global__ void k_ns_check(int W, int b, const float4* R, double* err, int* flag
     const double t = sqrt(block_sum_d((double)s, sh));
     if (threadIdx.x == 0) {
         const int e = bi % W;
-        const bool contracting = t < 0.5;
+        const bool num_ok = isfinite(t);
         if (step == 0) {
-            bad[bi] = contracting ? 0 : 1;
-            if (!contracting) {
+            // A seed that does not contract (|R| >= 0.5, or not finite) would
+            // need too many steps or diverge: the caller reseeds it in FP64.
+            const bool is_bad = (!num_ok) || (t >= 0.5);
+            bad[bi] = is_bad ? 1 : 0;
+            if (is_bad) {
                 atomicAdd(bad_count, 1);
                 atomicOr(flags + e, RGF_FLAG_REFINE);
             }
@@ -574,13 +577,13 @@ __global__ void k_ns_check(int W, int b, const float4* R, double* err, int* flag
         const bool more = !(t <= 3e-7);
         next_act[bi] = more ? 1 : 0;
         if (more && step == max_steps - 1) atomicOr(flags + e, RGF_FLAG_REFINE);
-        // Error estimate of the finished inverse: after the correction of this
-        // step the residual is about t^2; an entry that never got there
-        // reports its last residual.
+        // Error estimate of the finished inverse: after this step's correction
+        // the residual is about t^2; an entry that never got there reports
+        // its last residual.
         double est = -1.0;
         if (!more) est = t * t;
-        else if (step == max_steps - 1) est = (t == t) ? t : 1e300;
-        if (est >= 0.0 && (step > 0 || contracting))
+        else if (step == max_steps - 1) est = num_ok ? t : 1e300;
+        if (est >= 0.0)
             atomicMax(reinterpret_cast<unsigned long long*>(err + e), (unsigned long long)__double_as_longlong(est));
     }
 }
@@ -633,6 +636,70 @@ __global__ void k_mask_init(int batch, const int* act, int* out) {
 rgf_status mask_init(int batch, const int* act, int* out, cudaStream_t st) {
     if (batch <= 0) return RGF_OK;
     k_mask_init<<<ceil_div(batch, 256), 256, 0, st>>>(batch, act, out);
+    RGF_LAUNCH_CHECK();
+    return RGF_OK;
+}
+
+// kmax[i] = max(kmax[i], |g_i|_F |eps_i|_F) for active i (non-finite -> +inf):
+// an upper bound of the condition number of the matrix the decimation just
+// inverted.
+__global__ void k_dec_kmax(int b, const float4* g, const float4* eps, double* kmax, const int* act) {
+    const int bi = blockIdx.x;
+    if (act && !act[bi]) return;
+    __shared__ double sh[32];
+    const long nn = (long)b * b, off = (long)bi * nn;
+    float sg = 0.f, se = 0.f;
+    for (long i = threadIdx.x; i < nn; i += blockDim.x) {
+        const float4 a = g[off + i], c = eps[off + i];
+        sg = fmaf(a.x, a.x, fmaf(a.z, a.z, sg));
+        se = fmaf(c.x, c.x, fmaf(c.z, c.z, se));
+    }
+    const double tg = block_sum_d((double)sg, sh);
+    const double te = block_sum_d((double)se, sh);
+    if (threadIdx.x == 0) {
+        double k = sqrt(tg) * sqrt(te);
+        if (!isfinite(k)) k = INFINITY;
+        if (k > kmax[bi]) kmax[bi] = k;
+    }
+}
+
+rgf_status dec_kmax(int batch, int b, const float4* g, const float4* eps, double* kmax, const int* act,
+                    cudaStream_t st) {
+    if (batch <= 0) return RGF_OK;
+    k_dec_kmax<<<batch, 256, 0, st>>>(b, g, eps, kmax, act);
+    RGF_LAUNCH_CHECK();
+    return RGF_OK;
+}
+
+// redo[i] = kmax[i] > thr or not finite, or the decimation is still active;
+// counts them into *count.
+__global__ void k_dec_redo(int batch, const double* kmax, double thr, const int* still_active, int* redo,
+                           int* count) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= batch) return;
+    const double k = kmax[i];
+    const int r = (!(k <= thr) || still_active[i]) ? 1 : 0;
+    redo[i] = r;
+    if (r) atomicAdd(count, 1);
+}
+
+rgf_status dec_redo_mask(int batch, const double* kmax, double thr, const int* still_active, int* redo, int* count,
+                         cudaStream_t st) {
+    if (batch <= 0) return RGF_OK;
+    k_dec_redo<<<ceil_div(batch, 256), 256, 0, st>>>(batch, kmax, thr, still_active, redo, count);
+    RGF_LAUNCH_CHECK();
+    return RGF_OK;
+}
+
+// out[i] = sel[i] ? a[i] : b[i]
+__global__ void k_select_int(int batch, const int* sel, const int* a, const int* b, int* out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < batch) out[i] = sel[i] ? a[i] : b[i];
+}
+
+rgf_status select_int(int batch, const int* sel, const int* a, const int* b, int* out, cudaStream_t st) {
+    if (batch <= 0) return RGF_OK;
+    k_select_int<<<ceil_div(batch, 256), 256, 0, st>>>(batch, sel, a, b, out);
     RGF_LAUNCH_CHECK();
     return RGF_OK;
 }

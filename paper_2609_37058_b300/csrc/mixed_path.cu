@@ -4,6 +4,7 @@
 // X <- X + X (I - M X) whose residual and correction are again slice
 // products.  Matrices between kernels are double-float complex (float4).
 // The final Caroli trace is reduced in FP64.
+#include <cstdlib>
 #include <utility>
 #include <vector>
 
@@ -36,6 +37,14 @@ struct MixedState {
     int* h_bad = nullptr;   // pinned
     double2* c128 = nullptr;
     void* inv64_ws = nullptr;
+    // FP64 Sancho-Rubio redo of ill-conditioned lead decimations.
+    double2* dec64_pool = nullptr;
+    void* dec64_inv_ws = nullptr;
+    double* kmax = nullptr;      // 2W
+    int* redo = nullptr;         // 2W
+    int* act64 = nullptr;        // 2W
+    int* act_final = nullptr;    // 2W
+    double kmax_thr = 1e6;
     int core = 0;
 };
 
@@ -80,15 +89,17 @@ rgf_status mm(const Ctx& c, int cnt, int ia, int ib, float alpha, const float4* 
 // X = M^-1 for cnt matrices (batch entries i, energy i mod W): an FP32
 // Gauss-Jordan seed, then up to ns_steps Newton-Schulz steps X += X (I - M X)
 // in place, each entry stopping once its residual predicts convergence.
-// Entries whose FP32 seed does not contract (|I - M X|_F >= 0.5) are
-// reseeded with the FP64 Gauss-Jordan inverse before the first correction.
+// Entries whose seed residual is >= 0.5 are reseeded with the FP64
+// Gauss-Jordan inverse before the first correction.
 // Uses sa[1] for M, sa[0]/sb[0] for the steps and R as df scratch.
 rgf_status inv_mixed(const Ctx& c, int cnt, int W, const float4* M, float4* X, float4* R, const int* act,
                      int* gj_flags) {
     MixedState* m = c.m;
     rgf_plan_s* p = c.p;
     RGF_TRY(dfc_hi_to_c64(cnt, c.b, M, m->c64, act, c.st));
-    RGF_TRY(inv_t<float2>(cnt, c.b, m->c64, c.nn, m->inv_ws, gj_flags, act, c.st));
+    // An FP32 seed with a zero pivot is not reported: its residual is not
+    // finite, so it is reseeded in FP64 below, which reports its own pivots.
+    RGF_TRY(inv_t<float2>(cnt, c.b, m->c64, c.nn, m->inv_ws, nullptr, act, c.st));
     RGF_TRY(c64_to_dfc(cnt, c.b, m->c64, X, act, c.st));
     const int steps = p->opt.ns_steps;
     if (steps == 0) return RGF_OK;
@@ -131,6 +142,11 @@ size_t mixed_workspace_bytes(int W, int b) {
     s += (size_t)2 * W * nn * sizeof(double2) + inv_workspace_bytes_t<double2>(2 * W, b);
     s += (size_t)2 * W * b * sizeof(int) + (size_t)2 * W * 3 * sizeof(int) + 8192;
     return s;
+}
+
+size_t dec64_bytes(int W, int b) {
+    return (size_t)kDecMats * W * b * b * sizeof(double2) + inv_workspace_bytes_t<double2>(2 * W, b) + 1024 +
+           (size_t)2 * W * (sizeof(double) + 3 * sizeof(int));
 }
 
 rgf_status mixed_init(rgf_plan_s* p) {
@@ -194,6 +210,24 @@ rgf_status mixed_init(rgf_plan_s* p) {
                                  p->stream));
     RGF_TRY(alloc((void**)&m->status, sizeof(int)));
     RGF_TRY(alloc((void**)&m->bad_count, sizeof(int)));
+    {
+        char* d = nullptr;
+        RGF_TRY(alloc((void**)&d, dec64_bytes(W, b)));
+        m->dec64_pool = (double2*)d;
+        d += (size_t)kDecMats * W * nn * sizeof(double2);
+        m->dec64_inv_ws = (void*)d;
+        d += inv_workspace_bytes_t<double2>(2 * W, b);
+        d = (char*)(((uintptr_t)d + 255) & ~(uintptr_t)255);
+        m->kmax = (double*)d;
+        d += (size_t)2 * W * sizeof(double);
+        m->redo = (int*)d;
+        d += (size_t)2 * W * sizeof(int);
+        m->act64 = (int*)d;
+        d += (size_t)2 * W * sizeof(int);
+        m->act_final = (int*)d;
+        const char* thr = getenv("RGF_DEC_KMAX");
+        if (thr) m->kmax_thr = atof(thr);
+    }
     if (cudaMallocHost((void**)&m->h_bad, sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         set_error("mixed_init: cudaMallocHost failed");
@@ -215,6 +249,7 @@ void mixed_free(rgf_plan_s* p) {
         for (int k = 0; k < 6; ++k) cudaFree(m->lead[s][k]);
     cudaFree(m->status);
     cudaFree(m->bad_count);
+    cudaFree(m->dec64_pool);
     if (m->h_bad) cudaFreeHost(m->h_bad);
     delete m;
     p->mixed = nullptr;
@@ -276,9 +311,11 @@ rgf_status mixed_wave(rgf_plan_s* p, int W) {
         std::vector<int> ones(W2, 1);
         RGF_CUDA_TRY(cudaMemcpyAsync(p->d_active, ones.data(), sizeof(int) * W2, cudaMemcpyHostToDevice, st));
         RGF_CUDA_TRY(cudaMemsetAsync(p->d_iters, 0, sizeof(int) * W2, st));
+        RGF_CUDA_TRY(cudaMemsetAsync(m->kmax, 0, sizeof(double) * W2, st));
         int* act = p->d_active;
         for (int it = 1; it <= p->opt.dec_max_iter; ++it) {
             RGF_TRY(inv_mixed(c, W2, W, eps, g, R, act, p->d_dec_flags));
+            RGF_TRY(dec_kmax(W2, b, g, eps, m->kmax, act, st));
             RGF_TRY(sliceA(c, W2, 0, g, act));
             RGF_TRY(sliceB(c, W2, 0, alpha, act));
             RGF_TRY(mm(c, W2, 0, 0, 1.0f, nullptr, 0, ga, act));  // g alpha
@@ -302,9 +339,25 @@ rgf_status mixed_wave(rgf_plan_s* p, int W) {
             RGF_CUDA_TRY(cudaStreamSynchronize(st));
             if (*p->h_remaining == 0) break;
         }
-        RGF_TRY(merge_dec_flags(W, p->d_dec_flags, p->d_active, p->d_flags, st));
         RGF_TRY(inv_mixed(c, W2, W, eps_s, g, R, nullptr, p->d_dec_flags));
-        RGF_TRY(merge_dec_flags(W, p->d_dec_flags, p->d_active, p->d_flags, st));
+        RGF_TRY(dec_kmax(W2, b, g, eps_s, m->kmax, nullptr, st));
+        // Decimations whose intermediate inverses were ill-conditioned (or
+        // that did not converge) are redone in FP64: the double-float
+        // recursion loses about log10(kmax) of its ~14 digits there.
+        RGF_CUDA_TRY(cudaMemsetAsync(p->d_remaining, 0, sizeof(int), st));
+        RGF_TRY(dec_redo_mask(W2, m->kmax, m->kmax_thr, p->d_active, m->redo, p->d_remaining, st));
+        RGF_CUDA_TRY(cudaMemcpyAsync(p->h_remaining, p->d_remaining, sizeof(int), cudaMemcpyDeviceToHost, st));
+        RGF_CUDA_TRY(cudaStreamSynchronize(st));
+        if (*p->h_remaining > 0) {
+            p->n_dec_redo += *p->h_remaining;
+            double2* g64 = nullptr;
+            RGF_TRY(fp64_decimate(p, W, m->redo, m->dec64_pool, m->dec64_inv_ws, m->act64, &g64));
+            RGF_TRY(c128_to_dfc(W2, b, g64, g, m->redo, st));
+            RGF_TRY(select_int(W2, m->redo, m->act64, p->d_active, m->act_final, st));
+            RGF_TRY(merge_dec_flags(W, p->d_dec_flags, m->act_final, p->d_flags, st));
+        } else {
+            RGF_TRY(merge_dec_flags(W, p->d_dec_flags, p->d_active, p->d_flags, st));
+        }
     }
 
     // ---------------------------------------------------------- self-energies

@@ -46,6 +46,7 @@ struct rgf_plan_s {
     // Counters.
     long long n_waves = 0;
     long long n_reseeds = 0;
+    long long n_dec_redo = 0;
 
     // Mixed-path state (allocated only for RGF_MIXED).
     void* mixed = nullptr;
@@ -67,6 +68,10 @@ rgf_status run_transmission(rgf_plan_s* p, const double* E, int n_E, double* T, 
                             int* flags, int mem);
 // One wave, energies already in p->d_E[0..Wc); writes p->d_T, d_err, d_flags.
 rgf_status fp64_wave(rgf_plan_s* p, int Wc);
+// FP64 Sancho-Rubio for the masked (energy, lead) entries of one wave.
+rgf_status fp64_decimate(rgf_plan_s* p, int W, const int* mask, double2* pool, void* inv_ws, int* dec_active,
+                         double2** g_out);
+constexpr int kDecMats = 22;  // FP64 decimation matrices, in units of W
 rgf_status mixed_wave(rgf_plan_s* p, int Wc);
 size_t fp64_workspace_bytes(int W, int b);
 size_t mixed_workspace_bytes(int W, int b);

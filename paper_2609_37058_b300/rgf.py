@@ -71,7 +71,7 @@ def lib():
         "rgf_kernel_inverse_c64": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, _P]),
         "rgf_kernel_zgemm_mixed": (ctypes.c_int, [ctypes.c_int] * 4 + [_P, _P, _P, ctypes.c_int]),
         "rgf_launch_count": (ctypes.c_ulonglong, []),
-        "rgf_plan_stats": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),
+        "rgf_plan_stats": (ctypes.c_int, [_P] + [ctypes.POINTER(ctypes.c_longlong)] * 3),
         "rgf_gemm_timing": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)]),
     }
@@ -188,10 +188,10 @@ def rgf_plan_energy_wave(plan) -> int:
 
 
 def rgf_plan_stats(plan):
-    """(waves, fp64_reseeds) counted since the plan was created."""
-    w, r = ctypes.c_longlong(), ctypes.c_longlong()
-    _check(lib().rgf_plan_stats(plan, ctypes.byref(w), ctypes.byref(r)), "rgf_plan_stats")
-    return w.value, r.value
+    """(waves, fp64_reseeds, dec_fp64_redo) counted since the plan was created."""
+    w, r, d = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong()
+    _check(lib().rgf_plan_stats(plan, ctypes.byref(w), ctypes.byref(r), ctypes.byref(d)), "rgf_plan_stats")
+    return w.value, r.value, d.value
 
 
 def rgf_plan_destroy(plan):
@@ -259,7 +259,7 @@ def rgf_gemm_timing(enable: bool):
 class Plan:
     """Owns one rgf_plan_t.  ``precision`` is RGF_FP64 or RGF_MIXED."""
 
-    def __init__(self, n_layers, b, precision=RGF_FP64, eta=1e-6, energy_wave=0, ns_steps=4,
+    def __init__(self, n_layers, b, precision=RGF_FP64, eta=1e-6, energy_wave=0, ns_steps=6,
                  dec_tol=1e-14, dec_max_iter=100, cuda_stream=0):
         o = rgf_options_default()
         o.precision, o.eta, o.energy_wave, o.ns_steps = precision, eta, energy_wave, ns_steps

@@ -48,7 +48,7 @@ def test_every_declared_symbol_is_exported(L):
 def test_defaults_and_version(L):
     o = rgf.rgf_options_default()
     assert o.precision == rgf.RGF_FP64 and o.eta == 1e-6 and o.dec_tol == 1e-14
-    assert o.dec_max_iter == 100 and o.ns_steps == 4 and o.energy_wave == 0
+    assert o.dec_max_iter == 100 and o.ns_steps == 6 and o.energy_wave == 0
     assert "sm_103a" in rgf.rgf_version()
 
 

@@ -74,7 +74,7 @@ def test_junction_b128_sampled(rgf):
     idx = np.r_[0, 1, np.linspace(2, len(E) - 3, 6).astype(int), len(E) - 1]
     T, err, flags = run(rgf, dev, E[idx], eta)
     T_o = o.transmission(dev, E[idx], eta)
-    spread = fp64_uncertainty(dev, E[idx], eta, T_o, n_gauges=1)
+    spread = fp64_uncertainty(dev, E[idx], eta, T_o, n_gauges=3)
     assert np.all(flags == 0)
     d = np.abs(T - T_o)
     assert np.all(d <= fp64_bar(T_o, spread)), (d, d / T_o, spread)
@@ -145,7 +145,7 @@ def test_doped_b256_sampled(rgf):
     idx = np.array([0, 777, 1500, len(E) - 1])
     T, err, flags = run(rgf, dev, E[idx], eta)
     T_o = o.transmission(dev, E[idx], eta)
-    spread = fp64_uncertainty(dev, E[idx], eta, T_o, n_gauges=1)
+    spread = fp64_uncertainty(dev, E[idx], eta, T_o, n_gauges=3)
     assert np.all(flags == 0)
     d = np.abs(T - T_o)
     assert np.all(d <= fp64_bar(T_o, spread)), (d, d / T_o, spread)
