@@ -36,6 +36,31 @@ rgf_status rgf_kernel_inverse_c64(int batch, int b, float* A, int* flags);
 rgf_status rgf_kernel_zgemm_mixed(int batch, int m, int n, int k, const double* A, const double* B, double* C,
                                   int core);
 
+/* Allocation-free FP64 batched inverse.  The paper has no counterpart: this
+ * entry point exists for callers that cannot or must not allocate device
+ * memory, e.g. code running while another framework owns the device memory
+ * pool, or a latency-critical thread that cannot afford the implicit device
+ * synchronisation of cudaMalloc/cudaFree.  It inverts, in place, batch
+ * matrices b x b of complex128 values at the DEVICE pointer A (row-major
+ * (re, im) pairs, batch-major), with the same blocked Gauss-Jordan kernels
+ * as rgf_kernel_inverse_f64; flags (DEVICE pointer, may be NULL) receives
+ * RGF_FLAG_SINGULAR per matrix (it is cleared first).  The work is enqueued
+ * on cuda_stream (a cudaStream_t; NULL = legacy default stream) and the call
+ * returns without waiting for it.
+ *
+ * Scratch: a fixed file-scope device array of rgf_inverse_f64_noalloc_limit()
+ * bytes (16 MiB), present on every GPU that loads the library until the
+ * process exits.  A call whose workspace would exceed it (about 60 matrices
+ * of b = 256) is rejected with RGF_E_INVALID and a message.  The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress) and
+ * caches it; make that first call before any stream capture.  All calls on a
+ * device share the one array, which keeps the last call's contents, so calls
+ * that overlap on the GPU (different streams, no ordering) race. */
+rgf_status rgf_inverse_f64_noalloc(int batch, int b, double* A, int* flags, void* cuda_stream);
+
+/* Size in bytes of that fixed scratch array. */
+size_t rgf_inverse_f64_noalloc_limit(void);
+
 /* Counters for measurement (process-wide, thread-safe). */
 
 /* Number of CUDA kernel launches issued by the library since load. */

@@ -71,6 +71,8 @@ def lib():
         "rgf_kernel_inverse_c64": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, _P]),
         "rgf_kernel_zgemm_mixed": (ctypes.c_int, [ctypes.c_int] * 4 + [_P, _P, _P, ctypes.c_int]),
         "rgf_launch_count": (ctypes.c_ulonglong, []),
+        "rgf_inverse_f64_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, _P, _P]),
+        "rgf_inverse_f64_noalloc_limit": (ctypes.c_size_t, []),
         "rgf_plan_stats": (ctypes.c_int, [_P] + [ctypes.POINTER(ctypes.c_longlong)] * 3),
         "rgf_gemm_timing": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)]),
@@ -240,6 +242,24 @@ def rgf_kernel_inverse_c64(A):
     _check(lib().rgf_kernel_inverse_c64(X.shape[0], X.shape[1], X.ctypes.data, flags.ctypes.data),
            "rgf_kernel_inverse_c64")
     return X, flags
+
+
+def rgf_inverse_f64_noalloc(A, flags=None, cuda_stream=0):
+    """In-place FP64 inverses of the complex128 CUDA tensor A (batch, b, b)
+    with the library's fixed scratch array (no device allocation); flags is
+    an int32 CUDA tensor of batch entries or None.  Asynchronous on the
+    stream."""
+    pa, ma = _ptr(A, np.complex128)
+    pf, mf = _ptr(flags, np.int32)
+    if ma != RGF_MEM_DEVICE or (flags is not None and mf != RGF_MEM_DEVICE):
+        raise TypeError("rgf_inverse_f64_noalloc takes device tensors")
+    batch, b = int(A.shape[0]), int(A.shape[1])
+    _check(lib().rgf_inverse_f64_noalloc(batch, b, pa, pf, _P(cuda_stream) if cuda_stream else None),
+           "rgf_inverse_f64_noalloc")
+
+
+def rgf_inverse_f64_noalloc_limit() -> int:
+    return int(lib().rgf_inverse_f64_noalloc_limit())
 
 
 def rgf_launch_count() -> int:
