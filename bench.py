@@ -191,9 +191,10 @@ def main():
     err_d = torch.zeros(n_E, dtype=torch.float64, device="cuda")
     flags_d = torch.zeros(n_E, dtype=torch.int32, device="cuda")
 
+    from paper_2609_37058_b300.sharding import step_wave
+
     def wave(k):
-        start = ((k * world + rank) * W) % n_E
-        return start, min(W, n_E - start)
+        return step_wave(n_E, W, rank, world, k)
 
     def step(k):
         s, c = wave(k)
@@ -274,7 +275,7 @@ def main():
     h2d = dev.nbytes() + sum(getattr(l, f).nbytes for l in (dev.lead_L, dev.lead_R)
                              for f in ("H00", "S00", "H10", "S10", "Hc", "Sc")) + E_h.nbytes
     d2h = T_h.nbytes + err_h.nbytes + fl_h.nbytes
-    waves_done, reseeds, dec_redo = plan.stats
+    waves_done, reseeds = plan.stats
     plan.close()
 
     # ---------------------------------------------------------- FP64 GPU path
@@ -332,7 +333,6 @@ def main():
         "parity_sample": {"energies": nb, "max_abs_dT": float(dT.max()), "bar": 1e-6},
         "fp64_gpu": fp64,
         "fp64_reseeds": reseeds,
-        "fp64_decimation_redo": dec_redo,
         "flags_first_timed_wave": flag_counts,
         "clocks": clk,
     }

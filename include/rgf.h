@@ -147,11 +147,8 @@ rgf_status rgf_submit(rgf_plan_t plan, const double* E, int n_E, rgf_ticket_t* t
 rgf_status rgf_poll(rgf_ticket_t ticket, double* T, double* err, int* flags, int timeout_us);
 
 /* Counters of a plan since its creation (each output may be NULL): waves
- * run; mixed-path inverses whose FP32 seed was replaced by an FP64 seed; and
- * mixed-path lead decimations redone in FP64 because the double-float
- * recursion inverted matrices with condition estimate above 1e6 (or did not
- * converge). */
-rgf_status rgf_plan_stats(rgf_plan_t plan, long long* waves, long long* fp64_reseeds, long long* dec_fp64_redo);
+ * run, and mixed-path inverses whose FP32 seed was replaced by an FP64 seed. */
+rgf_status rgf_plan_stats(rgf_plan_t plan, long long* waves, long long* fp64_reseeds);
 
 /* Device bytes the plan holds (blocks + workspace for one energy wave). */
 rgf_status rgf_plan_device_bytes(rgf_plan_t plan, size_t* bytes);

@@ -36,6 +36,21 @@ rgf_status rgf_kernel_inverse_c64(int batch, int b, float* A, int* flags);
 rgf_status rgf_kernel_zgemm_mixed(int batch, int m, int n, int k, const double* A, const double* B, double* C,
                                   int core);
 
+/* Failure-path probe of the tcgen05 GEMM's bounded waits: runs a small
+ * slice-product GEMM whose producer skips the loads of the first K chunk,
+ * with every mbarrier wait limited to wait_us microseconds, so the waits
+ * run out.  Expected result: RGF_E_CUDA with *status_bits nonzero (bit 0x2:
+ * the MMA issuer gave up on data, 0x1: the producer gave up on a free
+ * stage), the CTAs having released their tensor memory; the context stays
+ * usable for the next call.  No GPU fault is involved. */
+rgf_status rgf_kernel_tc_timeout_probe(int wait_us, int* status_bits);
+
+/* C[i] = A[i] B[i] by the high-precision slice-product GEMM of the mixed
+ * path's lead decimation: FP64 operands split into seven BF16 slices (56
+ * bits relative to each row / column maximum), 28 products on the tcgen05
+ * tensor cores, FP64 result. */
+rgf_status rgf_kernel_zgemm_hp(int batch, int m, int n, int k, const double* A, const double* B, double* C);
+
 /* Allocation-free FP64 batched inverse.  The paper has no counterpart: this
  * entry point exists for callers that cannot or must not allocate device
  * memory, e.g. code running while another framework owns the device memory

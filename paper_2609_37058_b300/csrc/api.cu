@@ -242,11 +242,10 @@ rgf_status rgf_plan_device_bytes(rgf_plan_t p, size_t* bytes) {
     return RGF_OK;
 }
 
-rgf_status rgf_plan_stats(rgf_plan_t p, long long* waves, long long* fp64_reseeds, long long* dec_fp64_redo) {
+rgf_status rgf_plan_stats(rgf_plan_t p, long long* waves, long long* fp64_reseeds) {
     RGF_TRY(check_plan(p));
     if (waves) *waves = p->n_waves;
     if (fp64_reseeds) *fp64_reseeds = p->n_reseeds;
-    if (dec_fp64_redo) *dec_fp64_redo = p->n_dec_redo;
     return RGF_OK;
 }
 

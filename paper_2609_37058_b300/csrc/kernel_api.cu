@@ -111,8 +111,26 @@ rgf_status rgf_kernel_inverse_c64(int batch, int b, float* A, int* flags) {
     return RGF_OK;
 }
 
+static rgf_status zgemm_mixed_impl(int batch, int m, int n, int k, const double* A, const double* B, double* C,
+                                   int core, unsigned long long test_wait_ns, int* status_out);
+
 rgf_status rgf_kernel_zgemm_mixed(int batch, int m, int n, int k, const double* A, const double* B, double* C,
                                   int core) {
+    return zgemm_mixed_impl(batch, m, n, k, A, B, C, core, 0, nullptr);
+}
+
+rgf_status rgf_kernel_tc_timeout_probe(int wait_us, int* status_bits) {
+    if (wait_us < 1 || wait_us > 1000000 || !status_bits) {
+        rgf::set_error("rgf_kernel_tc_timeout_probe: wait_us in [1, 1e6] and a status pointer required");
+        return RGF_E_INVALID;
+    }
+    const int b = 64, batch = 2;
+    std::vector<double> A(2 * (size_t)batch * b * b, 0.5), B(2 * (size_t)batch * b * b, 0.25), C(2 * (size_t)batch * b * b);
+    return zgemm_mixed_impl(batch, b, b, b, A.data(), B.data(), C.data(), 0, 1000ull * wait_us, status_bits);
+}
+
+static rgf_status zgemm_mixed_impl(int batch, int m, int n, int k, const double* A, const double* B, double* C,
+                                   int core, unsigned long long test_wait_ns, int* status_out) {
     if (!dims_ok(batch, m, n, k) || !A || !B || !C || (core != 0 && core != 1)) {
         rgf::set_error("rgf_kernel_zgemm_mixed: invalid arguments");
         return RGF_E_INVALID;
@@ -154,9 +172,59 @@ rgf_status rgf_kernel_zgemm_mixed(int batch, int m, int n, int k, const double* 
     g.C = (float4*)fC.p;
     g.sC = (long)sc;
     g.status = (int*)status.p;
+    g.test_wait_ns = test_wait_ns;
     RGF_TRY(rgf::oz_gemm(g, core, 0));
     k_dfc_to_f64<<<1024, 256>>>((long)(batch * sc), (const float4*)fC.p, (double2*)dC.p);
     RGF_LAUNCH_CHECK();
+    int h_status = 0;
+    RGF_CUDA_TRY(cudaMemcpy(&h_status, status.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (status_out) *status_out = h_status;
+    if (h_status) {
+        rgf::set_error("tensor-core pipeline timeout (status 0x%x)", h_status);
+        return RGF_E_CUDA;
+    }
+    RGF_CUDA_TRY(cudaMemcpy(C, dC.p, batch * sc * 16, cudaMemcpyDeviceToHost));
+    return RGF_OK;
+}
+
+rgf_status rgf_kernel_zgemm_hp(int batch, int m, int n, int k, const double* A, const double* B, double* C) {
+    if (!dims_ok(batch, m, n, k) || !A || !B || !C) {
+        rgf::set_error("rgf_kernel_zgemm_hp: invalid arguments");
+        return RGF_E_INVALID;
+    }
+    if (batch == 0) return RGF_OK;
+    const size_t sa = (size_t)m * k, sb = (size_t)k * n, sc = (size_t)m * n;
+    const int Kp = rgf::slice_pitch(k);
+    DevBuf dA, dB, dC, SA, SB, cexp, status;
+    RGF_TRY(dalloc(dA, batch * sa * 16));
+    RGF_TRY(dalloc(dB, batch * sb * 16));
+    RGF_TRY(dalloc(dC, batch * sc * 16));
+    const size_t sab = (size_t)batch * rgf::kSlicesHP * m * Kp * 2, sbb = (size_t)batch * rgf::kSlicesHP * 2 * n * Kp * 2;
+    RGF_TRY(dalloc(SA, sab));
+    RGF_TRY(dalloc(SB, sbb));
+    RGF_TRY(dalloc(cexp, (size_t)batch * n * sizeof(int)));
+    RGF_TRY(dalloc(status, sizeof(int)));
+    RGF_CUDA_TRY(cudaMemset(SA.p, 0, sab));
+    RGF_CUDA_TRY(cudaMemset(SB.p, 0, sbb));
+    RGF_CUDA_TRY(cudaMemset(status.p, 0, sizeof(int)));
+    RGF_CUDA_TRY(cudaMemcpy(dA.p, A, batch * sa * 16, cudaMemcpyHostToDevice));
+    RGF_CUDA_TRY(cudaMemcpy(dB.p, B, batch * sb * 16, cudaMemcpyHostToDevice));
+    RGF_TRY(rgf::slice_rows_f64(batch, m, k, (const double2*)dA.p, (long)sa, (__nv_bfloat16*)SA.p, Kp, nullptr, 0));
+    RGF_TRY(rgf::slice_cols_f64(batch, k, n, (const double2*)dB.p, (long)sb, (__nv_bfloat16*)SB.p, Kp, (int*)cexp.p,
+                                nullptr, 0));
+    rgf::OzGemmHP g{};
+    g.batch = batch;
+    g.m = m;
+    g.n = n;
+    g.k = k;
+    g.As = (const __nv_bfloat16*)SA.p;
+    g.Bs = (const __nv_bfloat16*)SB.p;
+    g.Kp = Kp;
+    g.alpha = 1.0f;
+    g.C = (double2*)dC.p;
+    g.sC = (long)sc;
+    g.status = (int*)status.p;
+    RGF_TRY(rgf::oz_gemm_hp(g, 0));
     int h_status = 0;
     RGF_CUDA_TRY(cudaMemcpy(&h_status, status.p, sizeof(int), cudaMemcpyDeviceToHost));
     if (h_status) {

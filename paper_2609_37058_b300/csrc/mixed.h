@@ -27,6 +27,13 @@ constexpr int kSlices = 6;
 // K = 512, which is why five accumulators are kept.)
 constexpr int kGroups = 5;
 
+// High-precision variant for FP64 operands: seven balanced 8-bit digits
+// x = 2^e sum_{s=0..6} d_s 2^(-7-8s), |d_s| <= 128 (56 bits), 28 slice pairs,
+// groups 0..4 exact and the tail g = 5, 6 in a sixth accumulator (its
+// truncation is of order K * 13 * 2^-64 of the leading term); FP64 result.
+constexpr int kSlicesHP = 7;
+constexpr int kGroupsHP = 6;
+
 // Row pitch of a slice matrix in BF16 elements: real K = 2 k (re/im
 // interleaved) rounded up to a multiple of 64 so every 64-element chunk is
 // full; the padding is zero.
@@ -56,7 +63,32 @@ struct OzGemm {
     float4* C; long sC;
     const int* active;
     int* status;                 // device word, nonzero after a pipeline timeout
+    // Test hook (0 in normal use): nonzero makes the tcgen05 core skip the
+    // loads of the first K chunk and use this wait limit in nanoseconds, so
+    // that its bounded waits run out and report through *status.
+    unsigned long long test_wait_ns;
 };
+
+struct OzGemmHP {
+    int batch, m, n, k;          // complex sizes: C (m x n) = A (m x k) B (k x n)
+    const __nv_bfloat16* As;     // [batch][kSlicesHP][m][Kp]
+    const __nv_bfloat16* Bs;     // [batch][kSlicesHP][2n][Kp]
+    int Kp;
+    float alpha;                 // +1 or -1
+    const double2* D; long sD;   // optional FP64 addend (may alias C)
+    int add_identity;
+    double2* C; long sC;
+    const int* active;
+    int* status;
+};
+rgf_status oz_gemm_hp(const OzGemmHP& g, cudaStream_t st);
+// Seven-digit slicing of FP64 complex operands (layouts as slice_rows /
+// slice_cols with kSlicesHP planes); digits come from the FP64 bit pattern
+// by integer arithmetic.
+rgf_status slice_rows_f64(int batch, int m, int k, const double2* A, long sA, __nv_bfloat16* out, int Kp,
+                          const int* active, cudaStream_t st);
+rgf_status slice_cols_f64(int batch, int k, int n, const double2* B, long sB, __nv_bfloat16* out, int Kp,
+                          int* colexp, const int* active, cudaStream_t st);
 
 // Reference core on the legacy warp-level tensor path (mma.sync BF16).
 rgf_status oz_gemm_mma(const OzGemm& g, cudaStream_t st);
@@ -88,7 +120,10 @@ rgf_status gamma_dfc(int batch, int b, const float4* sigma, float4* gamma, cudaS
 rgf_status axpy_dfc(int batch, int b, float alpha, const float4* X, float4* Y, cudaStream_t st);
 // Newton-Schulz bookkeeping for step s of at most max_steps on batch
 // entries i (energy e = i mod W), given R = I - M X:
-//   step 0: entries with |R_i|_F >= 0.5 (or not finite) get bad[i] = 1,
+//   step 0: theta[i] = 1 / (1 - tr R_i) for a finite residual with
+//     |R_i|_F >= 0.5 (Sherman-Morrison scale of the first correction for a
+//     seed whose error is one near-singular direction), else 1;
+//   step 1: entries with |R_i|_F >= 0.5 (or not finite) get bad[i] = 1,
 //     are counted in *bad_count and flagged RGF_FLAG_REFINE; the caller
 //     reseeds them with an FP64 inverse;
 //   next_act[i] = act[i] && |R_i|_F > 3e-7 (after this step's correction
@@ -96,23 +131,25 @@ rgf_status axpy_dfc(int batch, int b, float alpha, const float4* X, float4* Y, c
 //   err[e] = max(err[e], estimated final residual); an entry still above
 //     3e-7 on the last step is flagged RGF_FLAG_REFINE.
 rgf_status ns_check(int batch, int W, int b, const float4* R, double* err, int* flags, int step, int max_steps,
-                    const int* act, int* next_act, int* bad, int* bad_count, cudaStream_t st);
+                    const int* act, int* next_act, int* bad, int* bad_count, double2* theta, cudaStream_t st);
+// R[i] *= theta[i] (complex) where theta[i] != 1.
+rgf_status scale_theta(int batch, int b, float4* R, const double2* theta, const int* act, cudaStream_t st);
+rgf_status ns_check_f64(int batch, int W, int b, const double2* R, double* err, int* flags, int step, int max_steps,
+                        const int* act, int* next_act, int* bad, int* bad_count, cudaStream_t st);
+rgf_status c128_to_c64(int batch, int b, const double2* X, float2* Y, const int* mask, cudaStream_t st);
+rgf_status c64_to_c128(int batch, int b, const float2* X, double2* Y, const int* mask, cudaStream_t st);
 // Masked conversions between df and FP64 complex (entries with mask[i]).
 rgf_status dfc_to_c128(int batch, int b, const float4* X, double2* Y, const int* mask, cudaStream_t st);
 rgf_status c128_to_dfc(int batch, int b, const double2* X, float4* Y, const int* mask, cudaStream_t st);
 // out[i] = act ? act[i] : 1
 rgf_status mask_init(int batch, const int* act, int* out, cudaStream_t st);
+rgf_status ns_check_f64(int batch, int W, int b, const double2* R, double* err, int* flags, int step, int max_steps,
+                        const int* act, int* next_act, int* bad, int* bad_count, cudaStream_t st);
+rgf_status c128_to_c64(int batch, int b, const double2* X, float2* Y, const int* mask, cudaStream_t st);
+rgf_status c64_to_c128(int batch, int b, const float2* X, double2* Y, const int* mask, cudaStream_t st);
 // Masked conversions between df and FP64 complex (entries with mask[i]).
 rgf_status dfc_to_c128(int batch, int b, const float4* X, double2* Y, const int* mask, cudaStream_t st);
 rgf_status c128_to_dfc(int batch, int b, const double2* X, float4* Y, const int* mask, cudaStream_t st);
-// Decimation conditioning: kmax[i] = max(kmax[i], |g_i|_F |eps_i|_F).
-rgf_status dec_kmax(int batch, int b, const float4* g, const float4* eps, double* kmax, const int* act,
-                    cudaStream_t st);
-// redo[i] = (kmax[i] > thr, or not finite, or still_active[i]); counted.
-rgf_status dec_redo_mask(int batch, const double* kmax, double thr, const int* still_active, int* redo, int* count,
-                         cudaStream_t st);
-// out[i] = sel[i] ? a[i] : b[i]
-rgf_status select_int(int batch, const int* sel, const int* a, const int* b, int* out, cudaStream_t st);
 // T[i] = Re sum X_jk conj(Y_jk) reduced in FP64 from df inputs.
 rgf_status trace_dfc(int batch, int b, const float4* X, const float4* Y, double* T, double* Ti, cudaStream_t st);
 

@@ -544,12 +544,13 @@ rgf_status axpy_dfc(int batch, int b, float alpha, const float4* X, float4* Y, c
 }
 
 __global__ void k_ns_check(int W, int b, const float4* R, double* err, int* flags, int step, int max_steps,
-                           const int* act, int* next_act, int* bad, int* bad_count) {
+                           const int* act, int* next_act, int* bad, int* bad_count, double2* theta) {
     const int bi = blockIdx.x;
     if (act && !act[bi]) {
         if (threadIdx.x == 0) {
             next_act[bi] = 0;
-            if (step == 0) bad[bi] = 0;
+            if (step <= 1) bad[bi] = 0;
+            if (step == 0) theta[bi] = make_double2(1.0, 0.0);
         }
         return;
     }
@@ -560,13 +561,37 @@ __global__ void k_ns_check(int W, int b, const float4* R, double* err, int* flag
         const float4 a = R[off + i];
         s = fmaf(a.x, a.x, fmaf(a.z, a.z, s));
     }
+    double tr_re = 0.0, tr_im = 0.0;
+    if (step == 0) {
+        for (int i = threadIdx.x; i < b; i += blockDim.x) {
+            const float4 a = R[off + (long)i * b + i];
+            tr_re += df_to_double(re_of(a));
+            tr_im += df_to_double(im_of(a));
+        }
+    }
     const double t = sqrt(block_sum_d((double)s, sh));
+    if (step == 0) {
+        tr_re = block_sum_d(tr_re, sh);
+        tr_im = block_sum_d(tr_im, sh);
+    }
     if (threadIdx.x == 0) {
         const int e = bi % W;
         const bool num_ok = isfinite(t);
         if (step == 0) {
-            // A seed that does not contract (|R| >= 0.5, or not finite) would
-            // need too many steps or diverge: the caller reseeds it in FP64.
+            // A seed that does not contract near a resonance has R = I - M X0
+            // dominated by one rank-1 term u v^H whose eigenvalue is about
+            // tr R; then (I - R)^-1 = I + R / (1 - tr R) (Sherman-Morrison) and
+            // the first correction is scaled by theta = 1 / (1 - tr R).  Other
+            // seeds keep theta = 1.
+            double2 th = make_double2(1.0, 0.0);
+            if (num_ok && t >= 0.5) {
+                const double dr = 1.0 - tr_re, di = -tr_im, d2 = dr * dr + di * di;
+                if (d2 > 1e-12) th = make_double2(dr / d2, -di / d2);
+            }
+            theta[bi] = th;
+        }
+        if (step == 1) {
+            // Entries that still do not contract are reseeded in FP64.
             const bool is_bad = (!num_ok) || (t >= 0.5);
             bad[bi] = is_bad ? 1 : 0;
             if (is_bad) {
@@ -589,9 +614,85 @@ __global__ void k_ns_check(int W, int b, const float4* R, double* err, int* flag
 }
 
 rgf_status ns_check(int batch, int W, int b, const float4* R, double* err, int* flags, int step, int max_steps,
-                    const int* act, int* next_act, int* bad, int* bad_count, cudaStream_t st) {
+                    const int* act, int* next_act, int* bad, int* bad_count, double2* theta, cudaStream_t st) {
     if (batch <= 0) return RGF_OK;
-    k_ns_check<<<batch, 256, 0, st>>>(W, b, R, err, flags, step, max_steps, act, next_act, bad, bad_count);
+    k_ns_check<<<batch, 256, 0, st>>>(W, b, R, err, flags, step, max_steps, act, next_act, bad, bad_count, theta);
+    RGF_LAUNCH_CHECK();
+    return RGF_OK;
+}
+
+// Same bookkeeping as k_ns_check for an FP64 residual.
+__global__ void k_ns_check_f64(int W, int b, const double2* R, double* err, int* flags, int step, int max_steps,
+                               const int* act, int* next_act, int* bad, int* bad_count) {
+    const int bi = blockIdx.x;
+    if (act && !act[bi]) {
+        if (threadIdx.x == 0) {
+            next_act[bi] = 0;
+            if (step == 0) bad[bi] = 0;
+        }
+        return;
+    }
+    __shared__ double sh[32];
+    const long nn = (long)b * b, off = (long)bi * nn;
+    double s = 0.0;
+    for (long i = threadIdx.x; i < nn; i += blockDim.x) {
+        const double2 a = R[off + i];
+        s += a.x * a.x + a.y * a.y;
+    }
+    const double t = sqrt(block_sum_d(s, sh));
+    if (threadIdx.x == 0) {
+        const int e = bi % W;
+        const bool num_ok = isfinite(t);
+        if (step == 0) {
+            const bool is_bad = (!num_ok) || (t >= 0.5);
+            bad[bi] = is_bad ? 1 : 0;
+            if (is_bad) {
+                atomicAdd(bad_count, 1);
+                atomicOr(flags + e, RGF_FLAG_REFINE);
+            }
+        }
+        const bool more = !(t <= 3e-7);
+        next_act[bi] = more ? 1 : 0;
+        if (more && step == max_steps - 1) atomicOr(flags + e, RGF_FLAG_REFINE);
+    }
+}
+
+rgf_status ns_check_f64(int batch, int W, int b, const double2* R, double* err, int* flags, int step, int max_steps,
+                        const int* act, int* next_act, int* bad, int* bad_count, cudaStream_t st) {
+    if (batch <= 0) return RGF_OK;
+    k_ns_check_f64<<<batch, 256, 0, st>>>(W, b, R, err, flags, step, max_steps, act, next_act, bad, bad_count);
+    RGF_LAUNCH_CHECK();
+    return RGF_OK;
+}
+
+__global__ void k_c128_to_c64(int b, const double2* X, float2* Y, const int* mask) {
+    if (mask && !mask[blockIdx.y]) return;
+    const long nn = (long)b * b, off = (long)blockIdx.y * nn;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += (long)gridDim.x * blockDim.x) {
+        const double2 v = X[off + i];
+        Y[off + i] = make_float2((float)v.x, (float)v.y);
+    }
+}
+
+rgf_status c128_to_c64(int batch, int b, const double2* X, float2* Y, const int* mask, cudaStream_t st) {
+    if (batch <= 0) return RGF_OK;
+    k_c128_to_c64<<<dim3(grid_for2((long)b * b, 256, 64), batch), 256, 0, st>>>(b, X, Y, mask);
+    RGF_LAUNCH_CHECK();
+    return RGF_OK;
+}
+
+__global__ void k_c64_to_c128(int b, const float2* X, double2* Y, const int* mask) {
+    if (mask && !mask[blockIdx.y]) return;
+    const long nn = (long)b * b, off = (long)blockIdx.y * nn;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += (long)gridDim.x * blockDim.x) {
+        const float2 v = X[off + i];
+        Y[off + i] = make_double2(v.x, v.y);
+    }
+}
+
+rgf_status c64_to_c128(int batch, int b, const float2* X, double2* Y, const int* mask, cudaStream_t st) {
+    if (batch <= 0) return RGF_OK;
+    k_c64_to_c128<<<dim3(grid_for2((long)b * b, 256, 64), batch), 256, 0, st>>>(b, X, Y, mask);
     RGF_LAUNCH_CHECK();
     return RGF_OK;
 }
@@ -628,6 +729,24 @@ rgf_status c128_to_dfc(int batch, int b, const double2* X, float4* Y, const int*
     return RGF_OK;
 }
 
+__global__ void k_scale_theta(int b, float4* R, const double2* theta, const int* act) {
+    const int bi = blockIdx.y;
+    if (act && !act[bi]) return;
+    const double2 th = theta[bi];
+    if (th.x == 1.0 && th.y == 0.0) return;
+    const float4 tf = cdf(df_from_double(th.x), df_from_double(th.y));
+    const long nn = (long)b * b, off = (long)bi * nn;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += (long)gridDim.x * blockDim.x)
+        R[off + i] = cdf_mul(R[off + i], tf);
+}
+
+rgf_status scale_theta(int batch, int b, float4* R, const double2* theta, const int* act, cudaStream_t st) {
+    if (batch <= 0) return RGF_OK;
+    k_scale_theta<<<dim3(grid_for2((long)b * b, 256, 64), batch), 256, 0, st>>>(b, R, theta, act);
+    RGF_LAUNCH_CHECK();
+    return RGF_OK;
+}
+
 __global__ void k_mask_init(int batch, const int* act, int* out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < batch) out[i] = act ? act[i] : 1;
@@ -636,70 +755,6 @@ __global__ void k_mask_init(int batch, const int* act, int* out) {
 rgf_status mask_init(int batch, const int* act, int* out, cudaStream_t st) {
     if (batch <= 0) return RGF_OK;
     k_mask_init<<<ceil_div(batch, 256), 256, 0, st>>>(batch, act, out);
-    RGF_LAUNCH_CHECK();
-    return RGF_OK;
-}
-
-// kmax[i] = max(kmax[i], |g_i|_F |eps_i|_F) for active i (non-finite -> +inf):
-// an upper bound of the condition number of the matrix the decimation just
-// inverted.
-__global__ void k_dec_kmax(int b, const float4* g, const float4* eps, double* kmax, const int* act) {
-    const int bi = blockIdx.x;
-    if (act && !act[bi]) return;
-    __shared__ double sh[32];
-    const long nn = (long)b * b, off = (long)bi * nn;
-    float sg = 0.f, se = 0.f;
-    for (long i = threadIdx.x; i < nn; i += blockDim.x) {
-        const float4 a = g[off + i], c = eps[off + i];
-        sg = fmaf(a.x, a.x, fmaf(a.z, a.z, sg));
-        se = fmaf(c.x, c.x, fmaf(c.z, c.z, se));
-    }
-    const double tg = block_sum_d((double)sg, sh);
-    const double te = block_sum_d((double)se, sh);
-    if (threadIdx.x == 0) {
-        double k = sqrt(tg) * sqrt(te);
-        if (!isfinite(k)) k = INFINITY;
-        if (k > kmax[bi]) kmax[bi] = k;
-    }
-}
-
-rgf_status dec_kmax(int batch, int b, const float4* g, const float4* eps, double* kmax, const int* act,
-                    cudaStream_t st) {
-    if (batch <= 0) return RGF_OK;
-    k_dec_kmax<<<batch, 256, 0, st>>>(b, g, eps, kmax, act);
-    RGF_LAUNCH_CHECK();
-    return RGF_OK;
-}
-
-// redo[i] = kmax[i] > thr or not finite, or the decimation is still active;
-// counts them into *count.
-__global__ void k_dec_redo(int batch, const double* kmax, double thr, const int* still_active, int* redo,
-                           int* count) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= batch) return;
-    const double k = kmax[i];
-    const int r = (!(k <= thr) || still_active[i]) ? 1 : 0;
-    redo[i] = r;
-    if (r) atomicAdd(count, 1);
-}
-
-rgf_status dec_redo_mask(int batch, const double* kmax, double thr, const int* still_active, int* redo, int* count,
-                         cudaStream_t st) {
-    if (batch <= 0) return RGF_OK;
-    k_dec_redo<<<ceil_div(batch, 256), 256, 0, st>>>(batch, kmax, thr, still_active, redo, count);
-    RGF_LAUNCH_CHECK();
-    return RGF_OK;
-}
-
-// out[i] = sel[i] ? a[i] : b[i]
-__global__ void k_select_int(int batch, const int* sel, const int* a, const int* b, int* out) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < batch) out[i] = sel[i] ? a[i] : b[i];
-}
-
-rgf_status select_int(int batch, const int* sel, const int* a, const int* b, int* out, cudaStream_t st) {
-    if (batch <= 0) return RGF_OK;
-    k_select_int<<<ceil_div(batch, 256), 256, 0, st>>>(batch, sel, a, b, out);
     RGF_LAUNCH_CHECK();
     return RGF_OK;
 }

@@ -37,19 +37,22 @@ struct MixedState {
     int* h_bad = nullptr;   // pinned
     double2* c128 = nullptr;
     void* inv64_ws = nullptr;
-    // FP64 Sancho-Rubio redo of ill-conditioned lead decimations.
-    double2* dec64_pool = nullptr;
-    void* dec64_inv_ws = nullptr;
-    double* kmax = nullptr;      // 2W
-    int* redo = nullptr;         // 2W
-    int* act64 = nullptr;        // 2W
-    int* act_final = nullptr;    // 2W
-    double kmax_thr = 1e6;
+    double2* theta = nullptr;  // 2W
+    // High-precision lead decimation: FP64 matrices and seven-slice buffers.
+    double2* dec_pool = nullptr;   // kDecUnits * W matrices
+    __nv_bfloat16* hsa[2] = {};
+    __nv_bfloat16* hsb[2] = {};
     int core = 0;
 };
 
-size_t sa_bytes(int cnt, int b, int Kp) { return (size_t)cnt * kSlices * b * Kp * sizeof(__nv_bfloat16); }
-size_t sb_bytes(int cnt, int b, int Kp) { return (size_t)cnt * kSlices * 2 * b * Kp * sizeof(__nv_bfloat16); }
+constexpr int kDecUnits = 24;  // FP64 decimation matrices, in units of W
+
+size_t sa_bytes(int cnt, int b, int Kp, int nsl = kSlices) {
+    return (size_t)cnt * nsl * b * Kp * sizeof(__nv_bfloat16);
+}
+size_t sb_bytes(int cnt, int b, int Kp, int nsl = kSlices) {
+    return (size_t)cnt * nsl * 2 * b * Kp * sizeof(__nv_bfloat16);
+}
 
 struct Ctx {
     MixedState* m;
@@ -86,11 +89,142 @@ rgf_status mm(const Ctx& c, int cnt, int ia, int ib, float alpha, const float4* 
     return oz_gemm(g, c.m->core, c.st);
 }
 
+// Seven-slice (FP64-class) counterparts for FP64 matrices.
+rgf_status hsliceA(const Ctx& c, int cnt, int ia, const double2* A, const int* act) {
+    return slice_rows_f64(cnt, c.b, c.b, A, c.nn, c.m->hsa[ia], c.m->Kp, act, c.st);
+}
+rgf_status hsliceB(const Ctx& c, int cnt, int ib, const double2* B, const int* act) {
+    return slice_cols_f64(cnt, c.b, c.b, B, c.nn, c.m->hsb[ib], c.m->Kp, c.m->colexp, act, c.st);
+}
+rgf_status hmm(const Ctx& c, int cnt, int ia, int ib, float alpha, const double2* D, int addI, double2* C,
+               const int* act) {
+    OzGemmHP g{};
+    g.batch = cnt;
+    g.m = g.n = g.k = c.b;
+    g.As = c.m->hsa[ia];
+    g.Bs = c.m->hsb[ib];
+    g.Kp = c.m->Kp;
+    g.alpha = alpha;
+    g.D = D;
+    g.sD = c.nn;
+    g.add_identity = addI;
+    g.C = C;
+    g.sC = c.nn;
+    g.active = act;
+    g.status = c.m->status;
+    return oz_gemm_hp(g, c.st);
+}
+
+// X = M^-1 for cnt FP64 matrices: FP32 Gauss-Jordan seed, then Newton-Schulz
+// steps with seven-slice products (FP64-class), FP64 Gauss-Jordan reseed of
+// seeds that do not contract.  Uses hsa[1] for M, hsa[0]/hsb[0] for the steps.
+rgf_status inv_hp(const Ctx& c, int cnt, int W, const double2* M, double2* X, double2* R, const int* act,
+                  int* gj_flags) {
+    MixedState* m = c.m;
+    rgf_plan_s* p = c.p;
+    RGF_TRY(c128_to_c64(cnt, c.b, M, m->c64, act, c.st));
+    RGF_TRY(inv_t<float2>(cnt, c.b, m->c64, c.nn, m->inv_ws, nullptr, act, c.st));
+    RGF_TRY(c64_to_c128(cnt, c.b, m->c64, X, act, c.st));
+    const int steps = p->opt.ns_steps;
+    if (steps == 0) return RGF_OK;
+    int* cur = m->nsact[0];
+    int* nxt = m->nsact[1];
+    RGF_TRY(mask_init(cnt, act, cur, c.st));
+    RGF_TRY(hsliceA(c, cnt, 1, M, act));
+    for (int s = 0; s < steps; ++s) {
+        RGF_TRY(hsliceB(c, cnt, 0, X, cur));
+        RGF_TRY(hmm(c, cnt, 1, 0, -1.0f, nullptr, 1, R, cur));  // R = I - M X
+        if (s == 0) RGF_CUDA_TRY(cudaMemsetAsync(m->bad_count, 0, sizeof(int), c.st));
+        RGF_TRY(ns_check_f64(cnt, W, c.b, R, p->d_err, p->d_flags, s, steps, cur, nxt, m->bad, m->bad_count, c.st));
+        if (s == 0) {
+            RGF_CUDA_TRY(cudaMemcpyAsync(m->h_bad, m->bad_count, sizeof(int), cudaMemcpyDeviceToHost, c.st));
+            RGF_CUDA_TRY(cudaStreamSynchronize(c.st));
+            if (*m->h_bad > 0) {
+                p->n_reseeds += *m->h_bad;
+                RGF_TRY(copy_f64(cnt, c.b, m->c128, M, m->bad, c.st));
+                RGF_TRY(inv_t<double2>(cnt, c.b, m->c128, c.nn, m->inv64_ws, gj_flags, m->bad, c.st));
+                RGF_TRY(copy_f64(cnt, c.b, X, m->c128, m->bad, c.st));
+                RGF_TRY(hsliceB(c, cnt, 0, X, m->bad));
+                RGF_TRY(hmm(c, cnt, 1, 0, -1.0f, nullptr, 1, R, m->bad));
+            }
+        }
+        RGF_TRY(hsliceA(c, cnt, 0, X, cur));
+        RGF_TRY(hsliceB(c, cnt, 0, R, cur));
+        RGF_TRY(hmm(c, cnt, 0, 0, 1.0f, X, 0, X, cur));  // X += X R
+        std::swap(cur, nxt);
+    }
+    return RGF_OK;
+}
+
+// Sancho-Rubio decimation of both leads with FP64 storage and seven-slice
+// products: batch entries s*W + e (s = 0 left, 1 right).  *g_out receives the
+// 2W surface Green's functions (FP64, inside the decimation pool).
+rgf_status hp_decimate(const Ctx& c, int W, double2** g_out) {
+    MixedState* m = c.m;
+    rgf_plan_s* p = c.p;
+    cudaStream_t st = c.st;
+    const int b = c.b, W2 = 2 * W;
+    const long nn = c.nn;
+    const double eta = p->opt.eta;
+    const double* E = p->d_E;
+    auto U = [&](int unit) { return m->dec_pool + (long)unit * W * nn; };
+    double2 *eps_s = U(0), *eps = U(2), *alpha = U(4), *beta = U(6), *g = U(8), *ga = U(10), *gb = U(12);
+    double2 *t1 = U(14), *t2 = U(16), *t3 = U(18), *t4 = U(20), *R = U(22);
+    double2** L = p->lead[0];
+    double2** Rl = p->lead[1];
+    {
+        FormSrc a{{L[1], Rl[1]}, {L[0], Rl[0]}, {0, 0}};
+        RGF_TRY(form_f64(W, 2, b, E, eta, a, eps, nullptr, 0.0, nullptr, st));
+        RGF_TRY(copy_f64(W2, b, eps_s, eps, nullptr, st));
+        // Outward coupling: left lead M_{j,j-1} (lower), right lead M_{j,j+1} (upper).
+        FormSrc al{{L[3], Rl[3]}, {L[2], Rl[2]}, {0, 1}};
+        FormSrc be{{L[3], Rl[3]}, {L[2], Rl[2]}, {1, 0}};
+        RGF_TRY(form_f64(W, 2, b, E, eta, al, alpha, nullptr, 0.0, nullptr, st));
+        RGF_TRY(form_f64(W, 2, b, E, eta, be, beta, nullptr, 0.0, nullptr, st));
+        RGF_TRY(fro_norm_f64(W2, b, eps, p->d_anorm, st));
+    }
+    std::vector<int> ones(W2, 1);
+    RGF_CUDA_TRY(cudaMemcpyAsync(p->d_active, ones.data(), sizeof(int) * W2, cudaMemcpyHostToDevice, st));
+    RGF_CUDA_TRY(cudaMemsetAsync(p->d_iters, 0, sizeof(int) * W2, st));
+    int* act = p->d_active;
+    for (int it = 1; it <= p->opt.dec_max_iter; ++it) {
+        RGF_TRY(inv_hp(c, W2, W, eps, g, R, act, p->d_dec_flags));
+        RGF_TRY(hsliceA(c, W2, 0, g, act));
+        RGF_TRY(hsliceB(c, W2, 0, alpha, act));
+        RGF_TRY(hmm(c, W2, 0, 0, 1.0f, nullptr, 0, ga, act));  // g alpha
+        RGF_TRY(hsliceB(c, W2, 1, beta, act));
+        RGF_TRY(hmm(c, W2, 0, 1, 1.0f, nullptr, 0, gb, act));  // g beta
+        RGF_TRY(hsliceB(c, W2, 0, gb, act));
+        RGF_TRY(hsliceB(c, W2, 1, ga, act));
+        RGF_TRY(hsliceA(c, W2, 0, alpha, act));
+        RGF_TRY(hmm(c, W2, 0, 0, 1.0f, nullptr, 0, t1, act));   // alpha g beta
+        RGF_TRY(hmm(c, W2, 0, 1, -1.0f, nullptr, 0, t3, act));  // -alpha g alpha
+        RGF_TRY(hsliceA(c, W2, 0, beta, act));
+        RGF_TRY(hmm(c, W2, 0, 1, 1.0f, nullptr, 0, t2, act));   // beta g alpha
+        RGF_TRY(hmm(c, W2, 0, 0, -1.0f, nullptr, 0, t4, act));  // -beta g beta
+        RGF_TRY(dec_update_f64(W2, b, eps_s, eps, t1, t2, act, st));
+        std::swap(alpha, t3);
+        std::swap(beta, t4);
+        RGF_CUDA_TRY(cudaMemsetAsync(p->d_remaining, 0, sizeof(int), st));
+        RGF_TRY(dec_check_f64(W2, b, alpha, beta, p->d_anorm, p->opt.dec_tol, it, act, p->d_iters, p->d_remaining,
+                              st));
+        RGF_CUDA_TRY(cudaMemcpyAsync(p->h_remaining, p->d_remaining, sizeof(int), cudaMemcpyDeviceToHost, st));
+        RGF_CUDA_TRY(cudaStreamSynchronize(st));
+        if (*p->h_remaining == 0) break;
+    }
+    RGF_TRY(merge_dec_flags(W, p->d_dec_flags, p->d_active, p->d_flags, st));
+    RGF_TRY(inv_hp(c, W2, W, eps_s, g, R, nullptr, p->d_dec_flags));
+    RGF_TRY(merge_dec_flags(W, p->d_dec_flags, p->d_active, p->d_flags, st));
+    *g_out = g;
+    return RGF_OK;
+}
+
 // X = M^-1 for cnt matrices (batch entries i, energy i mod W): an FP32
 // Gauss-Jordan seed, then up to ns_steps Newton-Schulz steps X += X (I - M X)
 // in place, each entry stopping once its residual predicts convergence.
-// Entries whose seed residual is >= 0.5 are reseeded with the FP64
-// Gauss-Jordan inverse before the first correction.
+// A seed whose residual is >= 0.5 gets a Sherman-Morrison-scaled first
+// correction (see ns_check); entries still at >= 0.5 after it are reseeded
+// with the FP64 Gauss-Jordan inverse.
 // Uses sa[1] for M, sa[0]/sb[0] for the steps and R as df scratch.
 rgf_status inv_mixed(const Ctx& c, int cnt, int W, const float4* M, float4* X, float4* R, const int* act,
                      int* gj_flags) {
@@ -110,9 +244,11 @@ rgf_status inv_mixed(const Ctx& c, int cnt, int W, const float4* M, float4* X, f
     for (int s = 0; s < steps; ++s) {
         RGF_TRY(sliceB(c, cnt, 0, X, cur));
         RGF_TRY(mm(c, cnt, 1, 0, -1.0f, nullptr, 1, R, cur));  // R = I - M X
-        if (s == 0) RGF_CUDA_TRY(cudaMemsetAsync(m->bad_count, 0, sizeof(int), c.st));
-        RGF_TRY(ns_check(cnt, W, c.b, R, p->d_err, p->d_flags, s, steps, cur, nxt, m->bad, m->bad_count, c.st));
-        if (s == 0) {
+        if (s == 1) RGF_CUDA_TRY(cudaMemsetAsync(m->bad_count, 0, sizeof(int), c.st));
+        RGF_TRY(ns_check(cnt, W, c.b, R, p->d_err, p->d_flags, s, steps, cur, nxt, m->bad, m->bad_count, m->theta,
+                         c.st));
+        if (s == 0) RGF_TRY(scale_theta(cnt, c.b, R, m->theta, cur, c.st));
+        if (s == 1) {
             RGF_CUDA_TRY(cudaMemcpyAsync(m->h_bad, m->bad_count, sizeof(int), cudaMemcpyDeviceToHost, c.st));
             RGF_CUDA_TRY(cudaStreamSynchronize(c.st));
             if (*m->h_bad > 0) {
@@ -140,13 +276,14 @@ size_t mixed_workspace_bytes(int W, int b) {
     s += 2 * sa_bytes(2 * W, b, Kp) + 2 * sb_bytes(2 * W, b, Kp);
     s += (size_t)2 * W * nn * sizeof(float2) + inv_workspace_bytes_t<float2>(2 * W, b);
     s += (size_t)2 * W * nn * sizeof(double2) + inv_workspace_bytes_t<double2>(2 * W, b);
-    s += (size_t)2 * W * b * sizeof(int) + (size_t)2 * W * 3 * sizeof(int) + 8192;
+    s += (size_t)2 * W * b * sizeof(int) + (size_t)2 * W * 3 * sizeof(int) + (size_t)2 * W * sizeof(double2) + 8192;
     return s;
 }
 
-size_t dec64_bytes(int W, int b) {
-    return (size_t)kDecMats * W * b * b * sizeof(double2) + inv_workspace_bytes_t<double2>(2 * W, b) + 1024 +
-           (size_t)2 * W * (sizeof(double) + 3 * sizeof(int));
+size_t dec_bytes(int W, int b) {
+    const int Kp = slice_pitch(b);
+    return (size_t)kDecUnits * W * b * b * sizeof(double2) + 2 * sa_bytes(2 * W, b, Kp, kSlicesHP) +
+           2 * sb_bytes(2 * W, b, Kp, kSlicesHP) + 1024;
 }
 
 rgf_status mixed_init(rgf_plan_s* p) {
@@ -203,6 +340,9 @@ rgf_status mixed_init(rgf_plan_s* p) {
     w += (size_t)2 * W * sizeof(int);
     m->bad = (int*)w;
     w += (size_t)2 * W * sizeof(int);
+    w = (char*)(((uintptr_t)w + 15) & ~(uintptr_t)15);
+    m->theta = (double2*)w;
+    w += (size_t)2 * W * sizeof(double2);
     w = (char*)(((uintptr_t)w + 255) & ~(uintptr_t)255);
     m->colexp = (int*)w;
     // Zero the slice buffers once: the K padding is never written again.
@@ -212,21 +352,21 @@ rgf_status mixed_init(rgf_plan_s* p) {
     RGF_TRY(alloc((void**)&m->bad_count, sizeof(int)));
     {
         char* d = nullptr;
-        RGF_TRY(alloc((void**)&d, dec64_bytes(W, b)));
-        m->dec64_pool = (double2*)d;
-        d += (size_t)kDecMats * W * nn * sizeof(double2);
-        m->dec64_inv_ws = (void*)d;
-        d += inv_workspace_bytes_t<double2>(2 * W, b);
-        d = (char*)(((uintptr_t)d + 255) & ~(uintptr_t)255);
-        m->kmax = (double*)d;
-        d += (size_t)2 * W * sizeof(double);
-        m->redo = (int*)d;
-        d += (size_t)2 * W * sizeof(int);
-        m->act64 = (int*)d;
-        d += (size_t)2 * W * sizeof(int);
-        m->act_final = (int*)d;
-        const char* thr = getenv("RGF_DEC_KMAX");
-        if (thr) m->kmax_thr = atof(thr);
+        RGF_TRY(alloc((void**)&d, dec_bytes(W, b)));
+        m->dec_pool = (double2*)d;
+        d += (size_t)kDecUnits * W * nn * sizeof(double2);
+        for (int i = 0; i < 2; ++i) {
+            m->hsa[i] = (__nv_bfloat16*)d;
+            d += sa_bytes(2 * W, b, m->Kp, kSlicesHP);
+        }
+        for (int i = 0; i < 2; ++i) {
+            m->hsb[i] = (__nv_bfloat16*)d;
+            d += sb_bytes(2 * W, b, m->Kp, kSlicesHP);
+        }
+        // The K padding of the slice buffers is never written: zero it once.
+        RGF_CUDA_TRY(cudaMemsetAsync(m->hsa[0], 0,
+                                     2 * sa_bytes(2 * W, b, m->Kp, kSlicesHP) + 2 * sb_bytes(2 * W, b, m->Kp, kSlicesHP),
+                                     p->stream));
     }
     if (cudaMallocHost((void**)&m->h_bad, sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
@@ -249,7 +389,7 @@ void mixed_free(rgf_plan_s* p) {
         for (int k = 0; k < 6; ++k) cudaFree(m->lead[s][k]);
     cudaFree(m->status);
     cudaFree(m->bad_count);
-    cudaFree(m->dec64_pool);
+    cudaFree(m->dec_pool);
     if (m->h_bad) cudaFreeHost(m->h_bad);
     delete m;
     p->mixed = nullptr;
@@ -293,71 +433,16 @@ rgf_status mixed_wave(rgf_plan_s* p, int W) {
     RGF_CUDA_TRY(cudaMemsetAsync(m->status, 0, sizeof(int), st));
 
     // ---------------------------------------------------------- decimation
-    float4 *eps_s = U(0), *eps = U(2), *alpha = U(4), *beta = U(6), *g = U(8), *ga = U(10), *gb = U(12);
-    float4 *t1 = U(14), *t2 = U(16), *t3 = U(18), *t4 = U(20), *R = U(22);
+    // Lead decimation runs with FP64 storage and seven-slice products: the
+    // Sancho-Rubio recursion inverts matrices with condition numbers up to
+    // ~1e7 at some energies and needs FP64-class arithmetic there.
+    float4 *g = U(8), *t1 = U(14), *t2 = U(16), *t3 = U(18);
     float4** L = m->lead[0];
     float4** Rl = m->lead[1];
     {
-        FormSrcDf a{{L[1], Rl[1]}, {L[0], Rl[0]}, {0, 0}};
-        RGF_TRY(form_dfc(W, 2, b, E, eta, a, eps, nullptr, nullptr, st));
-        RGF_TRY(copy_dfc(W2, b, eps_s, eps, nullptr, st));
-        FormSrcDf al{{L[3], Rl[3]}, {L[2], Rl[2]}, {0, 1}};
-        FormSrcDf be{{L[3], Rl[3]}, {L[2], Rl[2]}, {1, 0}};
-        RGF_TRY(form_dfc(W, 2, b, E, eta, al, alpha, nullptr, nullptr, st));
-        RGF_TRY(form_dfc(W, 2, b, E, eta, be, beta, nullptr, nullptr, st));
-        RGF_TRY(fro_norm_dfc(W2, b, eps, p->d_anorm, st));
-    }
-    {
-        std::vector<int> ones(W2, 1);
-        RGF_CUDA_TRY(cudaMemcpyAsync(p->d_active, ones.data(), sizeof(int) * W2, cudaMemcpyHostToDevice, st));
-        RGF_CUDA_TRY(cudaMemsetAsync(p->d_iters, 0, sizeof(int) * W2, st));
-        RGF_CUDA_TRY(cudaMemsetAsync(m->kmax, 0, sizeof(double) * W2, st));
-        int* act = p->d_active;
-        for (int it = 1; it <= p->opt.dec_max_iter; ++it) {
-            RGF_TRY(inv_mixed(c, W2, W, eps, g, R, act, p->d_dec_flags));
-            RGF_TRY(dec_kmax(W2, b, g, eps, m->kmax, act, st));
-            RGF_TRY(sliceA(c, W2, 0, g, act));
-            RGF_TRY(sliceB(c, W2, 0, alpha, act));
-            RGF_TRY(mm(c, W2, 0, 0, 1.0f, nullptr, 0, ga, act));  // g alpha
-            RGF_TRY(sliceB(c, W2, 1, beta, act));
-            RGF_TRY(mm(c, W2, 0, 1, 1.0f, nullptr, 0, gb, act));  // g beta
-            RGF_TRY(sliceB(c, W2, 0, gb, act));
-            RGF_TRY(sliceB(c, W2, 1, ga, act));
-            RGF_TRY(sliceA(c, W2, 0, alpha, act));
-            RGF_TRY(mm(c, W2, 0, 0, 1.0f, nullptr, 0, t1, act));   // alpha g beta
-            RGF_TRY(mm(c, W2, 0, 1, -1.0f, nullptr, 0, t3, act));  // -alpha g alpha
-            RGF_TRY(sliceA(c, W2, 0, beta, act));
-            RGF_TRY(mm(c, W2, 0, 1, 1.0f, nullptr, 0, t2, act));   // beta g alpha
-            RGF_TRY(mm(c, W2, 0, 0, -1.0f, nullptr, 0, t4, act));  // -beta g beta
-            RGF_TRY(dec_update_dfc(W2, b, eps_s, eps, t1, t2, act, st));
-            std::swap(alpha, t3);
-            std::swap(beta, t4);
-            RGF_CUDA_TRY(cudaMemsetAsync(p->d_remaining, 0, sizeof(int), st));
-            RGF_TRY(dec_check_dfc(W2, b, alpha, beta, p->d_anorm, p->opt.dec_tol, it, act, p->d_iters,
-                                  p->d_remaining, st));
-            RGF_CUDA_TRY(cudaMemcpyAsync(p->h_remaining, p->d_remaining, sizeof(int), cudaMemcpyDeviceToHost, st));
-            RGF_CUDA_TRY(cudaStreamSynchronize(st));
-            if (*p->h_remaining == 0) break;
-        }
-        RGF_TRY(inv_mixed(c, W2, W, eps_s, g, R, nullptr, p->d_dec_flags));
-        RGF_TRY(dec_kmax(W2, b, g, eps_s, m->kmax, nullptr, st));
-        // Decimations whose intermediate inverses were ill-conditioned (or
-        // that did not converge) are redone in FP64: the double-float
-        // recursion loses about log10(kmax) of its ~14 digits there.
-        RGF_CUDA_TRY(cudaMemsetAsync(p->d_remaining, 0, sizeof(int), st));
-        RGF_TRY(dec_redo_mask(W2, m->kmax, m->kmax_thr, p->d_active, m->redo, p->d_remaining, st));
-        RGF_CUDA_TRY(cudaMemcpyAsync(p->h_remaining, p->d_remaining, sizeof(int), cudaMemcpyDeviceToHost, st));
-        RGF_CUDA_TRY(cudaStreamSynchronize(st));
-        if (*p->h_remaining > 0) {
-            p->n_dec_redo += *p->h_remaining;
-            double2* g64 = nullptr;
-            RGF_TRY(fp64_decimate(p, W, m->redo, m->dec64_pool, m->dec64_inv_ws, m->act64, &g64));
-            RGF_TRY(c128_to_dfc(W2, b, g64, g, m->redo, st));
-            RGF_TRY(select_int(W2, m->redo, m->act64, p->d_active, m->act_final, st));
-            RGF_TRY(merge_dec_flags(W, p->d_dec_flags, m->act_final, p->d_flags, st));
-        } else {
-            RGF_TRY(merge_dec_flags(W, p->d_dec_flags, p->d_active, p->d_flags, st));
-        }
+        double2* g64 = nullptr;
+        RGF_TRY(hp_decimate(c, W, &g64));
+        RGF_TRY(c128_to_dfc(W2, b, g64, g, nullptr, st));
     }
 
     // ---------------------------------------------------------- self-energies

@@ -46,7 +46,6 @@ struct rgf_plan_s {
     // Counters.
     long long n_waves = 0;
     long long n_reseeds = 0;
-    long long n_dec_redo = 0;
 
     // Mixed-path state (allocated only for RGF_MIXED).
     void* mixed = nullptr;

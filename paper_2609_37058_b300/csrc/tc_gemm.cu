@@ -24,13 +24,26 @@
 namespace rgf {
 
 namespace {
-constexpr int TC_BM = 128, TC_BN = 96, TC_BK = 32;  // BK in BF16 elements (64 bytes)
+constexpr int TC_BM = 128, TC_BK = 32;  // BK in BF16 elements (64 bytes)
 constexpr int TC_STAGES = 2;
-constexpr int TC_ATILE = TC_BM * TC_BK * 2;                      // 8 KB per A slice tile
-constexpr int TC_BTILE = TC_BN * TC_BK * 2;                      // 6 KB per B slice tile
-constexpr int TC_STAGE_BYTES = kSlices * (TC_ATILE + TC_BTILE);  // 84 KB
-constexpr int TC_SMEM = TC_STAGES * TC_STAGE_BYTES + 1024 + 256;
 constexpr uint32_t TC_TMEM_COLS = 512;
+
+// Tile configuration of one kernel variant: NSL slices per operand, NGRP
+// TMEM accumulators (groups 0..NGRP-2 exact, the last one the tail), BN real
+// output columns per CTA (NGRP * BN <= 512 TMEM columns).
+template <int NSL, int NGRP, int BN>
+struct TcCfg {
+    static constexpr int ATILE = TC_BM * TC_BK * 2;        // 8 KB per A slice tile
+    static constexpr int BTILE = BN * TC_BK * 2;           // BN rows of 64 bytes
+    static constexpr int STAGE = NSL * (ATILE + BTILE);
+    static constexpr int SMEM = TC_STAGES * STAGE + 1024 + 256;
+    // Instruction descriptor: D = F32, A = B = BF16, both K-major, N = BN, M = 128.
+    static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                                      ((uint32_t)(TC_BM >> 4) << 24);
+    static_assert(NGRP * BN <= 512, "accumulators exceed TMEM");
+    static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "invalid N for M = 128");
+    static_assert(BTILE % 1024 == 0, "B tiles must keep 1024-byte alignment");
+};
 constexpr unsigned long long TC_WAIT_NS = 2000000000ull;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -59,13 +72,14 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 // Bounded wait: true when the phase completed, false (and status |= code)
-// after TC_WAIT_NS nanoseconds.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* status, int code) {
+// after limit_ns nanoseconds.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* status, int code,
+                                          unsigned long long limit_ns) {
     if (mbar_try(bar, parity)) return true;
     const unsigned long long t0 = globaltimer();
     for (unsigned it = 1;; ++it) {
         if (mbar_try(bar, parity)) return true;
-        if ((it & 255u) == 0 && globaltimer() - t0 > TC_WAIT_NS) {
+        if ((it & 255u) == 0 && globaltimer() - t0 > limit_ns) {
             atomicOr(status, code);
             return false;
         }
@@ -89,15 +103,11 @@ __device__ __forceinline__ uint64_t desc_sw64(uint32_t saddr) {
     d |= (uint64_t)4 << 61;              // 64-byte swizzle
     return d;
 }
-// Instruction descriptor: D = F32, A = B = BF16, both K-major, N = 96, M = 128.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_BN >> 3) << 17) |
-                            ((uint32_t)(TC_BM >> 4) << 24);
-
-__device__ __forceinline__ void umma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accum) {
+__device__ __forceinline__ void umma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
-        "l"(a), "l"(b), "r"(kIdesc), "r"(accum));
+        "l"(a), "l"(b), "r"(idesc), "r"(accum));
 }
 __device__ __forceinline__ void umma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
@@ -129,18 +139,41 @@ __device__ __forceinline__ float2 combine5(float g0, float g1, float g2, float g
 }
 }  // namespace
 
+// Arguments of one launch; C and D are float4 (double-float complex) for
+// the double-float variant and double2 for the FP64 variant.
+struct TcArgs {
+    int batch, m, n, k;
+    const __nv_bfloat16* As;
+    const __nv_bfloat16* Bs;
+    int Kp;
+    float alpha;
+    const void* D;
+    long sD;
+    int add_identity;
+    void* C;
+    long sC;
+    const int* active;
+    int* status;
+    // Failure-path test hooks: wait limit, and a producer that skips the
+    // loads of the first K chunk so that the pipeline's waits run out.
+    unsigned long long wait_ns;
+    int skip_first_chunk;
+};
+
+template <int NSL, int NGRP, int BN, bool OUT64>
 __global__ void __launch_bounds__(128, 1)
-    k_oz_tc(OzGemm g, const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB) {
+    k_oz_tc(TcArgs g, const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB) {
+    using Cfg = TcCfg<NSL, NGRP, BN>;
     const int bi = blockIdx.z;
     if (g.active && !g.active[bi]) return;
     extern __shared__ __align__(1024) unsigned char smem_tc[];
     unsigned char* base = (unsigned char*)(((uintptr_t)smem_tc + 1023) & ~(uintptr_t)1023);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(base + TC_STAGES * TC_STAGE_BYTES);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(base + TC_STAGES * Cfg::STAGE);
     // bars[0..1] full, bars[2..3] empty, bars[4] done; slot after them
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 8);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int m0 = blockIdx.y * TC_BM, n0 = blockIdx.x * TC_BN;
+    const int m0 = blockIdx.y * TC_BM, n0 = blockIdx.x * BN;
     const int nk = g.Kp / TC_BK;
     int* status = g.status;
 
@@ -164,16 +197,17 @@ __global__ void __launch_bounds__(128, 1)
         for (int kc = 0; kc < nk; ++kc) {
             const int s = kc & 1;
             if (kc >= TC_STAGES) {
-                if (!mbar_wait(smem_u32(&bars[2 + s]), ((kc >> 1) - 1) & 1, status, 0x1)) break;
+                if (!mbar_wait(smem_u32(&bars[2 + s]), ((kc >> 1) - 1) & 1, status, 0x1, g.wait_ns)) break;
             }
+            if (kc == 0 && g.skip_first_chunk) continue;
             const uint32_t fb = smem_u32(&bars[s]);
-            mbar_expect_tx(fb, TC_STAGE_BYTES);
-            unsigned char* st = base + s * TC_STAGE_BYTES;
+            mbar_expect_tx(fb, Cfg::STAGE);
+            unsigned char* st = base + s * Cfg::STAGE;
 #pragma unroll
-            for (int sl = 0; sl < kSlices; ++sl) {
-                tma_load_3d(smem_u32(st + sl * TC_ATILE), &tmA, kc * TC_BK, m0, bi * kSlices + sl, fb);
-                tma_load_3d(smem_u32(st + kSlices * TC_ATILE + sl * TC_BTILE), &tmB, kc * TC_BK, n0,
-                            bi * kSlices + sl, fb);
+            for (int sl = 0; sl < NSL; ++sl) {
+                tma_load_3d(smem_u32(st + sl * Cfg::ATILE), &tmA, kc * TC_BK, m0, bi * NSL + sl, fb);
+                tma_load_3d(smem_u32(st + NSL * Cfg::ATILE + sl * Cfg::BTILE), &tmB, kc * TC_BK, n0, bi * NSL + sl,
+                            fb);
             }
         }
     } else if (tid == 32) {
@@ -181,26 +215,26 @@ __global__ void __launch_bounds__(128, 1)
         bool ok = true;
         for (int kc = 0; kc < nk && ok; ++kc) {
             const int s = kc & 1;
-            if (!mbar_wait(smem_u32(&bars[s]), (kc >> 1) & 1, status, 0x2)) {
+            if (!mbar_wait(smem_u32(&bars[s]), (kc >> 1) & 1, status, 0x2, g.wait_ns)) {
                 ok = false;
                 break;
             }
             tc_fence_after();
-            unsigned char* st = base + s * TC_STAGE_BYTES;
-            const uint32_t a0 = smem_u32(st), b0 = smem_u32(st + kSlices * TC_ATILE);
+            unsigned char* st = base + s * Cfg::STAGE;
+            const uint32_t a0 = smem_u32(st), b0 = smem_u32(st + NSL * Cfg::ATILE);
             uint32_t started = 0;
 #pragma unroll
-            for (int i = 0; i < kSlices; ++i) {
+            for (int i = 0; i < NSL; ++i) {
 #pragma unroll
-                for (int j = 0; j < kSlices; ++j) {
-                    if (i + j > kSlices - 1) continue;
-                    const int grp = (i + j) < (kGroups - 1) ? (i + j) : (kGroups - 1);
+                for (int j = 0; j < NSL; ++j) {
+                    if (i + j > NSL - 1) continue;
+                    const int grp = (i + j) < (NGRP - 1) ? (i + j) : (NGRP - 1);
 #pragma unroll
                     for (int kk = 0; kk < TC_BK / 16; ++kk) {
-                        const uint64_t ad = desc_sw64(a0 + i * TC_ATILE + kk * 32);
-                        const uint64_t bd = desc_sw64(b0 + j * TC_BTILE + kk * 32);
+                        const uint64_t ad = desc_sw64(a0 + i * Cfg::ATILE + kk * 32);
+                        const uint64_t bd = desc_sw64(b0 + j * Cfg::BTILE + kk * 32);
                         const uint32_t acc = (kc > 0 || (started >> grp) & 1u) ? 1u : 0u;
-                        umma(taddr + (uint32_t)(grp * TC_BN), ad, bd, acc);
+                        umma(taddr + (uint32_t)(grp * BN), ad, bd, Cfg::IDESC, acc);
                         started |= 1u << grp;
                     }
                 }
@@ -211,11 +245,11 @@ __global__ void __launch_bounds__(128, 1)
     }
     __syncwarp();
 
-    // ---------------- epilogue: TMEM -> registers -> df -> global
+    // ---------------- epilogue: TMEM -> registers -> result -> global
     // One lane per warp waits; the outcome is made warp-uniform because the
     // TMEM loads below are warp-collective.
     int done_i = 0;
-    if (lane == 0) done_i = mbar_wait(smem_u32(&bars[4]), 0, status, 0x4) ? 1 : 0;
+    if (lane == 0) done_i = mbar_wait(smem_u32(&bars[4]), 0, status, 0x4, g.wait_ns) ? 1 : 0;
     const bool done = __shfl_sync(0xffffffffu, done_i, 0) != 0;
     __syncwarp();
     tc_fence_after();
@@ -223,18 +257,38 @@ __global__ void __launch_bounds__(128, 1)
         const int r = m0 + warp * 32 + lane;
         const uint32_t trow = taddr + ((uint32_t)(warp * 32) << 16);
 #pragma unroll 1
-        for (int q = 0; q < TC_BN / 16; ++q) {
-            float v[kGroups][16];
+        for (int q = 0; q < BN / 16; ++q) {
+            float v[NGRP][16];
 #pragma unroll
-            for (int gq = 0; gq < kGroups; ++gq) tmem_ld16(trow + gq * TC_BN + q * 16, v[gq]);
+            for (int gq = 0; gq < NGRP; ++gq) tmem_ld16(trow + gq * BN + q * 16, v[gq]);
             tmem_ld_wait();
             if (r < g.m) {
                 const int c0 = (n0 + q * 16) >> 1;
-                float4* out = g.C + (long)bi * g.sC + (long)r * g.n;
 #pragma unroll
                 for (int t = 0; t < 8; ++t) {
                     const int c = c0 + t;
-                    if (c < g.n) {
+                    if (c >= g.n) continue;
+                    const long o = (long)bi * g.sC + (long)r * g.n + c;
+                    if constexpr (OUT64) {
+                        // Sum the groups in FP64, smallest first.
+                        double re = 0.0, im = 0.0;
+#pragma unroll
+                        for (int gq = NGRP - 1; gq >= 0; --gq) {
+                            re += (double)v[gq][2 * t];
+                            im += (double)v[gq][2 * t + 1];
+                        }
+                        if (g.alpha < 0.0f) {
+                            re = -re;
+                            im = -im;
+                        }
+                        if (g.D) {
+                            const double2 d = reinterpret_cast<const double2*>(g.D)[(long)bi * g.sD + (long)r * g.n + c];
+                            re += d.x;
+                            im += d.y;
+                        }
+                        if (g.add_identity && r == c) re += 1.0;
+                        reinterpret_cast<double2*>(g.C)[o] = make_double2(re, im);
+                    } else {
                         float2 re = combine5(v[0][2 * t], v[1][2 * t], v[2][2 * t], v[3][2 * t], v[4][2 * t]);
                         float2 im = combine5(v[0][2 * t + 1], v[1][2 * t + 1], v[2][2 * t + 1], v[3][2 * t + 1],
                                              v[4][2 * t + 1]);
@@ -243,12 +297,12 @@ __global__ void __launch_bounds__(128, 1)
                             im = df_neg(im);
                         }
                         if (g.D) {
-                            const float4 d = g.D[(long)bi * g.sD + (long)r * g.n + c];
+                            const float4 d = reinterpret_cast<const float4*>(g.D)[(long)bi * g.sD + (long)r * g.n + c];
                             re = df_add(re, re_of(d));
                             im = df_add(im, im_of(d));
                         }
                         if (g.add_identity && r == c) re = df_add(re, make_float2(1.0f, 0.0f));
-                        out[c] = cdf(re, im);
+                        reinterpret_cast<float4*>(g.C)[o] = cdf(re, im);
                     }
                 }
             }
@@ -258,7 +312,7 @@ __global__ void __launch_bounds__(128, 1)
     __syncthreads();
     if (!done && tid == 0) {
         // Drain TMA copies that may still be in flight before the CTA exits.
-        for (int s = 0; s < TC_STAGES; ++s) mbar_wait(smem_u32(&bars[s]), 0, status, 0x8);
+        for (int s = 0; s < TC_STAGES; ++s) mbar_wait(smem_u32(&bars[s]), 0, status, 0x8, g.wait_ns);
     }
     __syncthreads();
     if (warp == 1) {
@@ -303,37 +357,56 @@ static rgf_status encode_slices(CUtensorMap* map, const __nv_bfloat16* ptr, int 
     return RGF_OK;
 }
 
-rgf_status oz_gemm_tc(const OzGemm& g, cudaStream_t st) {
+template <int NSL, int NGRP, int BN, bool OUT64>
+static rgf_status launch_tc(const TcArgs& g, cudaStream_t st) {
+    using Cfg = TcCfg<NSL, NGRP, BN>;
     if (g.batch <= 0) return RGF_OK;
     if (g.Kp % TC_BK != 0 || ((uintptr_t)g.As & 15) || ((uintptr_t)g.Bs & 15) || !g.status) {
         set_error("oz_gemm_tc: bad slice layout");
         return RGF_E_INVALID;
     }
-    if (g.batch > 65535 || (long)g.batch * kSlices > 0x7fffffffL) {
+    if (g.batch > 65535 || (long)g.batch * NSL > 0x7fffffffL) {
         set_error("oz_gemm_tc: batch too large");
         return RGF_E_INVALID;
     }
     CUtensorMap ta, tb;
-    RGF_TRY(encode_slices(&ta, g.As, g.Kp, g.m, (long)g.batch * kSlices, TC_BM));
-    RGF_TRY(encode_slices(&tb, g.Bs, g.Kp, 2L * g.n, (long)g.batch * kSlices, TC_BN));
+    RGF_TRY(encode_slices(&ta, g.As, g.Kp, g.m, (long)g.batch * NSL, TC_BM));
+    RGF_TRY(encode_slices(&tb, g.Bs, g.Kp, 2L * g.n, (long)g.batch * NSL, BN));
     static bool attr = false;
     if (!attr) {
-        RGF_CUDA_TRY(cudaFuncSetAttribute(k_oz_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+        RGF_CUDA_TRY(cudaFuncSetAttribute(k_oz_tc<NSL, NGRP, BN, OUT64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          Cfg::SMEM));
         attr = true;
     }
-    dim3 grid(ceil_div(2L * g.n, TC_BN), ceil_div(g.m, TC_BM), g.batch);
+    dim3 grid(ceil_div(2L * g.n, BN), ceil_div(g.m, TC_BM), g.batch);
     // Only unmasked launches are timed: their work is exactly known.
     const bool timed = gemm_timing_enabled() && g.active == nullptr;
     cudaEvent_t ev = nullptr;
     if (timed) gemm_timing_before(st, &ev);
-    k_oz_tc<<<grid, 128, TC_SMEM, st>>>(g, ta, tb);
+    k_oz_tc<NSL, NGRP, BN, OUT64><<<grid, 128, Cfg::SMEM, st>>>(g, ta, tb);
     RGF_LAUNCH_CHECK();
     if (timed) {
-        // 21 slice-pair real products of M = m, N = 2n, K = 2k per batch entry.
-        const double pairs = (double)(kSlices * (kSlices + 1) / 2);
+        // NSL(NSL+1)/2 slice-pair real products of M = m, N = 2n, K = 2k per batch entry.
+        const double pairs = (double)(NSL * (NSL + 1) / 2);
         gemm_timing_after(st, ev, pairs * 2.0 * g.m * (2.0 * g.n) * (2.0 * g.k) * g.batch);
     }
     return RGF_OK;
+}
+
+rgf_status oz_gemm_tc(const OzGemm& g, cudaStream_t st) {
+    TcArgs a{g.batch, g.m, g.n, g.k, g.As, g.Bs, g.Kp, g.alpha, g.D, g.sD, g.add_identity, g.C, g.sC, g.active,
+             g.status, TC_WAIT_NS, 0};
+    if (g.test_wait_ns) {
+        a.wait_ns = g.test_wait_ns;
+        a.skip_first_chunk = 1;
+    }
+    return launch_tc<kSlices, kGroups, 96, false>(a, st);
+}
+
+rgf_status oz_gemm_hp(const OzGemmHP& g, cudaStream_t st) {
+    TcArgs a{g.batch, g.m, g.n, g.k, g.As, g.Bs, g.Kp, g.alpha, g.D, g.sD, g.add_identity, g.C, g.sC, g.active,
+             g.status, TC_WAIT_NS, 0};
+    return launch_tc<kSlicesHP, kGroupsHP, 80, true>(a, st);
 }
 
 }  // namespace rgf

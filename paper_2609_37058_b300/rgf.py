@@ -71,9 +71,11 @@ def lib():
         "rgf_kernel_inverse_c64": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, _P]),
         "rgf_kernel_zgemm_mixed": (ctypes.c_int, [ctypes.c_int] * 4 + [_P, _P, _P, ctypes.c_int]),
         "rgf_launch_count": (ctypes.c_ulonglong, []),
+        "rgf_kernel_zgemm_hp": (ctypes.c_int, [ctypes.c_int] * 4 + [_P, _P, _P]),
+        "rgf_kernel_tc_timeout_probe": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
         "rgf_inverse_f64_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, _P, _P]),
         "rgf_inverse_f64_noalloc_limit": (ctypes.c_size_t, []),
-        "rgf_plan_stats": (ctypes.c_int, [_P] + [ctypes.POINTER(ctypes.c_longlong)] * 3),
+        "rgf_plan_stats": (ctypes.c_int, [_P] + [ctypes.POINTER(ctypes.c_longlong)] * 2),
         "rgf_gemm_timing": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)]),
     }
@@ -190,10 +192,10 @@ def rgf_plan_energy_wave(plan) -> int:
 
 
 def rgf_plan_stats(plan):
-    """(waves, fp64_reseeds, dec_fp64_redo) counted since the plan was created."""
-    w, r, d = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong()
-    _check(lib().rgf_plan_stats(plan, ctypes.byref(w), ctypes.byref(r), ctypes.byref(d)), "rgf_plan_stats")
-    return w.value, r.value, d.value
+    """(waves, fp64_reseeds) counted since the plan was created."""
+    w, r = ctypes.c_longlong(), ctypes.c_longlong()
+    _check(lib().rgf_plan_stats(plan, ctypes.byref(w), ctypes.byref(r)), "rgf_plan_stats")
+    return w.value, r.value
 
 
 def rgf_plan_destroy(plan):
@@ -225,6 +227,23 @@ def rgf_kernel_zgemm_mixed(A, B, core=0):
     _check(lib().rgf_kernel_zgemm_mixed(batch, m, n, k, _host(A, np.complex128), _host(B, np.complex128),
                                         C.ctypes.data, int(core)), "rgf_kernel_zgemm_mixed")
     return C
+
+
+def rgf_kernel_zgemm_hp(A, B):
+    """C[i] = A[i] B[i] with the seven-slice (FP64-class) tensor-core GEMM."""
+    batch, m, k = A.shape
+    n = B.shape[2]
+    C = np.empty((batch, m, n), dtype=np.complex128)
+    _check(lib().rgf_kernel_zgemm_hp(batch, m, n, k, _host(A, np.complex128), _host(B, np.complex128),
+                                     C.ctypes.data), "rgf_kernel_zgemm_hp")
+    return C
+
+
+def rgf_kernel_tc_timeout_probe(wait_us=20000):
+    """Returns (status, status_bits) of the bounded-wait probe (see header)."""
+    bits = ctypes.c_int(0)
+    st = lib().rgf_kernel_tc_timeout_probe(int(wait_us), ctypes.byref(bits))
+    return st, bits.value
 
 
 def rgf_kernel_inverse_f64(A):

@@ -55,6 +55,32 @@ def test_zgemm_mixed(rgf, core, batch, m, n, k):
     assert np.all(err <= bound), (err / bound).max()
 
 
+@pytest.mark.parametrize("batch,m,n,k", SHAPES)
+def test_zgemm_hp(rgf, batch, m, n, k):
+    """Seven slices keep 56 bits of each entry relative to its row/column
+    maximum; every product is then within ~k 2^-53 of rowmax * colmax."""
+    rng = np.random.default_rng(m + 5 * k)
+    A, B = crand(rng, batch, m, k), crand(rng, batch, k, n)
+    A[:, ::3, :] *= 1e-5
+    B[:, :, ::4] *= 1e4
+    C = rgf.rgf_kernel_zgemm_hp(A, B)
+    ref = A @ B
+    k_ = A.shape[2]
+    ra = np.maximum(np.abs(A.real), np.abs(A.imag)).max(axis=2)[:, :, None]
+    cb = np.maximum(np.abs(B.real), np.abs(B.imag)).max(axis=1)[:, None, :]
+    bound = 4.0 * k_ * 2.0 ** -53 * ra * cb
+    err = np.abs(C - ref)
+    assert np.all(err <= bound), (err / bound).max()
+
+
+def test_zgemm_hp_exact_integers(rgf):
+    rng = np.random.default_rng(3)
+    A = rng.integers(-1000, 1001, (2, 64, 256)) + 1j * rng.integers(-1000, 1001, (2, 64, 256))
+    B = rng.integers(-1000, 1001, (2, 256, 40)) + 1j * rng.integers(-1000, 1001, (2, 256, 40))
+    C = rgf.rgf_kernel_zgemm_hp(A.astype(np.complex128), B.astype(np.complex128))
+    assert np.array_equal(C, A @ B)
+
+
 def test_mixed_cores_agree(rgf):
     rng = np.random.default_rng(5)
     A, B = crand(rng, 3, 256, 256), crand(rng, 3, 256, 256)
@@ -90,3 +116,14 @@ def test_inverse_c64(rgf, b):
     X, flags = rgf.rgf_kernel_inverse_c64(A)
     r = np.abs(X.astype(np.complex128) @ A.astype(np.complex128) - np.eye(b)).max()
     assert np.all(flags == 0) and r < 1e-4
+
+
+def test_tc_bounded_waits_report_and_recover(rgf):
+    """A pipeline whose loads never arrive ends by its wait limit with an
+    error status, and the next GEMM on the same context is correct."""
+    st, bits = rgf.rgf_kernel_tc_timeout_probe(20000)
+    assert st == rgf.RGF_E_CUDA and bits != 0
+    rng = np.random.default_rng(9)
+    A, B = crand(rng, 2, 64, 64), crand(rng, 2, 64, 64)
+    C = rgf.rgf_kernel_zgemm_mixed(A, B, core=0)
+    assert np.all(np.abs(C - A @ B) <= mixed_bound(A, B))
