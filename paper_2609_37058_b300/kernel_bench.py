@@ -1,0 +1,74 @@
+"""Kernel-level driver: runs one library kernel entry point on a seeded batch.
+
+    python -m paper_2609_37058_b300.kernel_bench --op mixed --batch 148 --b 256 --reps 2
+
+Ops: ``mixed`` (six-slice double-float GEMM), ``hp`` (seven-slice FP64-class
+GEMM), ``f64`` (FP64 CUDA-core GEMM), ``inv64`` / ``inv32`` (batched
+Gauss-Jordan inverses).  Each repetition is one call of the C entry point
+(host buffers in and out).  The call prints one JSON line with the wall time
+per call and the largest deviation from numpy's own product or inverse, so
+that the command is a self-checking target for profilers.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+
+from . import rgf
+
+
+def _inputs(op: str, batch: int, b: int, seed: int):
+    rng = np.random.default_rng(seed)
+
+    def cplx(shape):
+        return (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)) / np.sqrt(2.0)
+
+    if op in ("inv64", "inv32"):
+        # Diagonally weighted so that every matrix is well conditioned.
+        A = cplx((batch, b, b)) / np.sqrt(b) + 2.0 * np.eye(b)
+        return (A,)
+    return cplx((batch, b, b)), cplx((batch, b, b))
+
+
+def run(op: str, batch: int, b: int, reps: int, seed: int = 0) -> dict:
+    args = _inputs(op, batch, b, seed)
+    fn = {
+        "mixed": lambda: rgf.rgf_kernel_zgemm_mixed(*args, core=0),
+        "hp": lambda: rgf.rgf_kernel_zgemm_hp(*args),
+        "f64": lambda: rgf.rgf_kernel_zgemm_f64(*args),
+        "inv64": lambda: rgf.rgf_kernel_inverse_f64(*args)[0],
+        "inv32": lambda: rgf.rgf_kernel_inverse_c64(args[0].astype(np.complex64))[0],
+    }[op]
+    out = None
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        out = fn()
+    dt = (time.perf_counter() - t0) / max(reps, 1)
+    if op in ("inv64", "inv32"):
+        dev = float(np.abs(np.matmul(args[0], out.astype(np.complex128)) - np.eye(b)).max())
+        what = "max |A X - I|"
+    else:
+        dev = float(np.abs(out - np.matmul(*args)).max())
+        what = "max |C - A B|"
+    return {"op": op, "batch": batch, "b": b, "reps": reps, "s_per_call": dt, "check": what, "value": dev}
+
+
+def main(argv=None) -> int:
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--op", choices=["mixed", "hp", "f64", "inv64", "inv32"], default="mixed")
+    ap.add_argument("--batch", type=int, default=148)
+    ap.add_argument("--b", type=int, default=256)
+    ap.add_argument("--reps", type=int, default=2)
+    ap.add_argument("--seed", type=int, default=0)
+    a = ap.parse_args(argv)
+    res = run(a.op, a.batch, a.b, a.reps, a.seed)
+    print(json.dumps(res))
+    limit = {"mixed": 1e-9, "hp": 1e-12, "f64": 1e-12, "inv64": 1e-10, "inv32": 1e-3}[a.op]
+    return 0 if res["value"] <= limit * max(1.0, np.sqrt(a.b)) else 1
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())
