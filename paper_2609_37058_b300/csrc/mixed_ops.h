@@ -1,0 +1,98 @@
+// Mixed-precision workspace and the composite operations built on the
+// slice-product GEMMs: refined inverses and Sancho-Rubio decimation.  Used by
+// the single-device plan and by the multi-device server.
+#pragma once
+
+#include "mixed.h"
+
+namespace rgf {
+
+constexpr int kPoolUnits = 24;  // df matrices, in units of W
+constexpr int kDecUnits = 24;   // FP64 decimation matrices, in units of W
+
+// Workspace of W energies (2W lead entries) of block size b.
+struct MixedState {
+    int b = 0, W = 0, Kp = 0;
+    float4* pool = nullptr;  // kPoolUnits * W df matrices
+    __nv_bfloat16* sa[2] = {};
+    __nv_bfloat16* sb[2] = {};
+    int* colexp = nullptr;
+    float2* c64 = nullptr;
+    void* inv_ws = nullptr;
+    int* status = nullptr;   // tcgen05 pipeline timeout word
+    int* nsact[2] = {};
+    int* bad = nullptr;
+    int* bad_count = nullptr;
+    int* h_bad = nullptr;    // pinned
+    double2* c128 = nullptr;
+    void* inv64_ws = nullptr;
+    double2* theta = nullptr;  // 2W
+    // High-precision lead decimation: FP64 matrices and seven-slice buffers.
+    double2* dec_pool = nullptr;  // kDecUnits * W matrices
+    __nv_bfloat16* hsa[2] = {};
+    __nv_bfloat16* hsb[2] = {};
+    // Decimation bookkeeping (2W entries each).
+    int* dec_active = nullptr;
+    int* dec_iters = nullptr;
+    int* dec_flags = nullptr;
+    double* dec_anorm = nullptr;
+    int* dec_remaining = nullptr;
+    int* h_remaining = nullptr;  // pinned
+    int core = 0;                // 0 = tcgen05, 1 = mma.sync reference core
+    void* own = nullptr;         // allocation owned by the state (when ws was not given)
+    void* dec_own = nullptr;
+};
+
+// Bytes of the carved workspace (without the decimation pool).
+size_t mixed_workspace_bytes(int W, int b);
+// Bytes of the decimation pool and its slice buffers.
+size_t mixed_dec_bytes(int W, int b);
+// Set up m for W energies of block size b.  ws (mixed_workspace_bytes) may be
+// null, in which case the state allocates it.  The decimation pool and the
+// small buffers are always allocated by the state.
+rgf_status mixed_state_init(MixedState* m, int b, int W, void* ws, cudaStream_t st);
+void mixed_state_free(MixedState* m);
+
+// What one batch of refined inverses writes besides X.
+struct Ctx {
+    MixedState* m;
+    cudaStream_t st;
+    long nn;
+    int b;
+    int ns_steps;
+    double* err;           // per energy (entry i -> energy i mod W)
+    int* flags;            // per energy
+    long long* n_reseeds;  // host counter
+};
+
+// Slice A by rows into sa[ia], B by columns into sb[ib]; C = alpha A B (+ D) (+ I).
+rgf_status sliceA(const Ctx& c, int cnt, int ia, const float4* A, const int* act);
+rgf_status sliceB(const Ctx& c, int cnt, int ib, const float4* B, const int* act);
+rgf_status mm(const Ctx& c, int cnt, int ia, int ib, float alpha, const float4* D, int addI, float4* C,
+              const int* act);
+// Seven-slice (FP64-class) counterparts for FP64 matrices.
+rgf_status hsliceA(const Ctx& c, int cnt, int ia, const double2* A, const int* act);
+rgf_status hsliceB(const Ctx& c, int cnt, int ib, const double2* B, const int* act);
+rgf_status hmm(const Ctx& c, int cnt, int ia, int ib, float alpha, const double2* D, int addI, double2* C,
+               const int* act);
+
+// X = M^-1 (df) for cnt entries: FP32 seed, Newton-Schulz refinement with a
+// Sherman-Morrison-scaled first step, FP64 reseed of entries that do not
+// contract.  R is df scratch of cnt matrices.
+rgf_status inv_mixed(const Ctx& c, int cnt, int W, const float4* M, float4* X, float4* R, const int* act,
+                     int* gj_flags);
+// The same for FP64 matrices with seven-slice products.
+rgf_status inv_hp(const Ctx& c, int cnt, int W, const double2* M, double2* X, double2* R, const int* act,
+                  int* gj_flags);
+
+// Decimation pool unit u (u*W matrices in).  Units 0, 2, 4, 6 hold eps_s,
+// eps, alpha, beta of the 2W entries (s*W + e, s = side) on entry to
+// hp_decimate_run.
+inline double2* dec_unit(const MixedState* m, int W, int u) { return m->dec_pool + (long)u * W * m->b * m->b; }
+// Sancho-Rubio decimation of the 2W lead entries already formed in units
+// 0, 2, 4, 6 (FP64 storage, seven-slice products).  *g_out receives the 2W
+// surface Green's functions; per-energy flags (c.flags) get the decimation's
+// NOCONV and SINGULAR bits.
+rgf_status hp_decimate_run(const Ctx& c, int W, double tol, int max_iter, double2** g_out);
+
+}  // namespace rgf

@@ -9,43 +9,21 @@
 #include <vector>
 
 #include "gj_tmpl.cuh"
-#include "mixed.h"
+#include "mixed_ops.h"
 #include "plan.h"
 
 namespace rgf {
 
 namespace {
-constexpr int kPoolUnits = 24;  // df matrices, in units of W
-
-struct MixedState {
-    int b = 0, W = 0, Kp = 0;
+// Device Hamiltonian of a plan in double-float, plus its workspace.
+struct PlanMixed {
+    MixedState ms;
     float4* H_diag = nullptr;
     float4* S_diag = nullptr;
     float4* H_lower = nullptr;
     float4* S_lower = nullptr;
     float4* lead[2][6] = {};
-    float4* pool = nullptr;
-    __nv_bfloat16* sa[2] = {};
-    __nv_bfloat16* sb[2] = {};
-    int* colexp = nullptr;
-    float2* c64 = nullptr;
-    void* inv_ws = nullptr;
-    int* status = nullptr;
-    int* nsact[2] = {};
-    int* bad = nullptr;
-    int* bad_count = nullptr;
-    int* h_bad = nullptr;   // pinned
-    double2* c128 = nullptr;
-    void* inv64_ws = nullptr;
-    double2* theta = nullptr;  // 2W
-    // High-precision lead decimation: FP64 matrices and seven-slice buffers.
-    double2* dec_pool = nullptr;   // kDecUnits * W matrices
-    __nv_bfloat16* hsa[2] = {};
-    __nv_bfloat16* hsb[2] = {};
-    int core = 0;
 };
-
-constexpr int kDecUnits = 24;  // FP64 decimation matrices, in units of W
 
 size_t sa_bytes(int cnt, int b, int Kp, int nsl = kSlices) {
     return (size_t)cnt * nsl * b * Kp * sizeof(__nv_bfloat16);
@@ -53,14 +31,7 @@ size_t sa_bytes(int cnt, int b, int Kp, int nsl = kSlices) {
 size_t sb_bytes(int cnt, int b, int Kp, int nsl = kSlices) {
     return (size_t)cnt * nsl * 2 * b * Kp * sizeof(__nv_bfloat16);
 }
-
-struct Ctx {
-    MixedState* m;
-    rgf_plan_s* p;
-    cudaStream_t st;
-    long nn;
-    int b;
-};
+}  // namespace
 
 // Slice A by rows into sa[ia], B by columns into sb[ib].
 rgf_status sliceA(const Ctx& c, int cnt, int ia, const float4* A, const int* act) {
@@ -121,11 +92,10 @@ rgf_status hmm(const Ctx& c, int cnt, int ia, int ib, float alpha, const double2
 rgf_status inv_hp(const Ctx& c, int cnt, int W, const double2* M, double2* X, double2* R, const int* act,
                   int* gj_flags) {
     MixedState* m = c.m;
-    rgf_plan_s* p = c.p;
     RGF_TRY(c128_to_c64(cnt, c.b, M, m->c64, act, c.st));
     RGF_TRY(inv_t<float2>(cnt, c.b, m->c64, c.nn, m->inv_ws, nullptr, act, c.st));
     RGF_TRY(c64_to_c128(cnt, c.b, m->c64, X, act, c.st));
-    const int steps = p->opt.ns_steps;
+    const int steps = c.ns_steps;
     if (steps == 0) return RGF_OK;
     int* cur = m->nsact[0];
     int* nxt = m->nsact[1];
@@ -135,12 +105,12 @@ rgf_status inv_hp(const Ctx& c, int cnt, int W, const double2* M, double2* X, do
         RGF_TRY(hsliceB(c, cnt, 0, X, cur));
         RGF_TRY(hmm(c, cnt, 1, 0, -1.0f, nullptr, 1, R, cur));  // R = I - M X
         if (s == 0) RGF_CUDA_TRY(cudaMemsetAsync(m->bad_count, 0, sizeof(int), c.st));
-        RGF_TRY(ns_check_f64(cnt, W, c.b, R, p->d_err, p->d_flags, s, steps, cur, nxt, m->bad, m->bad_count, c.st));
+        RGF_TRY(ns_check_f64(cnt, W, c.b, R, c.err, c.flags, s, steps, cur, nxt, m->bad, m->bad_count, c.st));
         if (s == 0) {
             RGF_CUDA_TRY(cudaMemcpyAsync(m->h_bad, m->bad_count, sizeof(int), cudaMemcpyDeviceToHost, c.st));
             RGF_CUDA_TRY(cudaStreamSynchronize(c.st));
             if (*m->h_bad > 0) {
-                p->n_reseeds += *m->h_bad;
+                if (c.n_reseeds) *c.n_reseeds += *m->h_bad;
                 RGF_TRY(copy_f64(cnt, c.b, m->c128, M, m->bad, c.st));
                 RGF_TRY(inv_t<double2>(cnt, c.b, m->c128, c.nn, m->inv64_ws, gj_flags, m->bad, c.st));
                 RGF_TRY(copy_f64(cnt, c.b, X, m->c128, m->bad, c.st));
@@ -156,39 +126,23 @@ rgf_status inv_hp(const Ctx& c, int cnt, int W, const double2* M, double2* X, do
     return RGF_OK;
 }
 
-// Sancho-Rubio decimation of both leads with FP64 storage and seven-slice
-// products: batch entries s*W + e (s = 0 left, 1 right).  *g_out receives the
-// 2W surface Green's functions (FP64, inside the decimation pool).
-rgf_status hp_decimate(const Ctx& c, int W, double2** g_out) {
+// Sancho-Rubio decimation of the 2W lead entries formed in units 0, 2, 4, 6
+// of the decimation pool, with FP64 storage and seven-slice products.
+rgf_status hp_decimate_run(const Ctx& c, int W, double tol, int max_iter, double2** g_out) {
     MixedState* m = c.m;
-    rgf_plan_s* p = c.p;
     cudaStream_t st = c.st;
     const int b = c.b, W2 = 2 * W;
-    const long nn = c.nn;
-    const double eta = p->opt.eta;
-    const double* E = p->d_E;
-    auto U = [&](int unit) { return m->dec_pool + (long)unit * W * nn; };
+    auto U = [&](int unit) { return dec_unit(m, W, unit); };
     double2 *eps_s = U(0), *eps = U(2), *alpha = U(4), *beta = U(6), *g = U(8), *ga = U(10), *gb = U(12);
     double2 *t1 = U(14), *t2 = U(16), *t3 = U(18), *t4 = U(20), *R = U(22);
-    double2** L = p->lead[0];
-    double2** Rl = p->lead[1];
-    {
-        FormSrc a{{L[1], Rl[1]}, {L[0], Rl[0]}, {0, 0}};
-        RGF_TRY(form_f64(W, 2, b, E, eta, a, eps, nullptr, 0.0, nullptr, st));
-        RGF_TRY(copy_f64(W2, b, eps_s, eps, nullptr, st));
-        // Outward coupling: left lead M_{j,j-1} (lower), right lead M_{j,j+1} (upper).
-        FormSrc al{{L[3], Rl[3]}, {L[2], Rl[2]}, {0, 1}};
-        FormSrc be{{L[3], Rl[3]}, {L[2], Rl[2]}, {1, 0}};
-        RGF_TRY(form_f64(W, 2, b, E, eta, al, alpha, nullptr, 0.0, nullptr, st));
-        RGF_TRY(form_f64(W, 2, b, E, eta, be, beta, nullptr, 0.0, nullptr, st));
-        RGF_TRY(fro_norm_f64(W2, b, eps, p->d_anorm, st));
-    }
+    RGF_TRY(fro_norm_f64(W2, b, eps, m->dec_anorm, st));
     std::vector<int> ones(W2, 1);
-    RGF_CUDA_TRY(cudaMemcpyAsync(p->d_active, ones.data(), sizeof(int) * W2, cudaMemcpyHostToDevice, st));
-    RGF_CUDA_TRY(cudaMemsetAsync(p->d_iters, 0, sizeof(int) * W2, st));
-    int* act = p->d_active;
-    for (int it = 1; it <= p->opt.dec_max_iter; ++it) {
-        RGF_TRY(inv_hp(c, W2, W, eps, g, R, act, p->d_dec_flags));
+    RGF_CUDA_TRY(cudaMemcpyAsync(m->dec_active, ones.data(), sizeof(int) * W2, cudaMemcpyHostToDevice, st));
+    RGF_CUDA_TRY(cudaMemsetAsync(m->dec_iters, 0, sizeof(int) * W2, st));
+    RGF_CUDA_TRY(cudaMemsetAsync(m->dec_flags, 0, sizeof(int) * W2, st));
+    int* act = m->dec_active;
+    for (int it = 1; it <= max_iter; ++it) {
+        RGF_TRY(inv_hp(c, W2, W, eps, g, R, act, m->dec_flags));
         RGF_TRY(hsliceA(c, W2, 0, g, act));
         RGF_TRY(hsliceB(c, W2, 0, alpha, act));
         RGF_TRY(hmm(c, W2, 0, 0, 1.0f, nullptr, 0, ga, act));  // g alpha
@@ -205,16 +159,15 @@ rgf_status hp_decimate(const Ctx& c, int W, double2** g_out) {
         RGF_TRY(dec_update_f64(W2, b, eps_s, eps, t1, t2, act, st));
         std::swap(alpha, t3);
         std::swap(beta, t4);
-        RGF_CUDA_TRY(cudaMemsetAsync(p->d_remaining, 0, sizeof(int), st));
-        RGF_TRY(dec_check_f64(W2, b, alpha, beta, p->d_anorm, p->opt.dec_tol, it, act, p->d_iters, p->d_remaining,
-                              st));
-        RGF_CUDA_TRY(cudaMemcpyAsync(p->h_remaining, p->d_remaining, sizeof(int), cudaMemcpyDeviceToHost, st));
+        RGF_CUDA_TRY(cudaMemsetAsync(m->dec_remaining, 0, sizeof(int), st));
+        RGF_TRY(dec_check_f64(W2, b, alpha, beta, m->dec_anorm, tol, it, act, m->dec_iters, m->dec_remaining, st));
+        RGF_CUDA_TRY(cudaMemcpyAsync(m->h_remaining, m->dec_remaining, sizeof(int), cudaMemcpyDeviceToHost, st));
         RGF_CUDA_TRY(cudaStreamSynchronize(st));
-        if (*p->h_remaining == 0) break;
+        if (*m->h_remaining == 0) break;
     }
-    RGF_TRY(merge_dec_flags(W, p->d_dec_flags, p->d_active, p->d_flags, st));
-    RGF_TRY(inv_hp(c, W2, W, eps_s, g, R, nullptr, p->d_dec_flags));
-    RGF_TRY(merge_dec_flags(W, p->d_dec_flags, p->d_active, p->d_flags, st));
+    RGF_TRY(merge_dec_flags(W, m->dec_flags, m->dec_active, c.flags, st));
+    RGF_TRY(inv_hp(c, W2, W, eps_s, g, R, nullptr, m->dec_flags));
+    RGF_TRY(merge_dec_flags(W, m->dec_flags, m->dec_active, c.flags, st));
     *g_out = g;
     return RGF_OK;
 }
@@ -229,13 +182,12 @@ rgf_status hp_decimate(const Ctx& c, int W, double2** g_out) {
 rgf_status inv_mixed(const Ctx& c, int cnt, int W, const float4* M, float4* X, float4* R, const int* act,
                      int* gj_flags) {
     MixedState* m = c.m;
-    rgf_plan_s* p = c.p;
     RGF_TRY(dfc_hi_to_c64(cnt, c.b, M, m->c64, act, c.st));
     // An FP32 seed with a zero pivot is not reported: its residual is not
     // finite, so it is reseeded in FP64 below, which reports its own pivots.
     RGF_TRY(inv_t<float2>(cnt, c.b, m->c64, c.nn, m->inv_ws, nullptr, act, c.st));
     RGF_TRY(c64_to_dfc(cnt, c.b, m->c64, X, act, c.st));
-    const int steps = p->opt.ns_steps;
+    const int steps = c.ns_steps;
     if (steps == 0) return RGF_OK;
     int* cur = m->nsact[0];
     int* nxt = m->nsact[1];
@@ -245,14 +197,13 @@ rgf_status inv_mixed(const Ctx& c, int cnt, int W, const float4* M, float4* X, f
         RGF_TRY(sliceB(c, cnt, 0, X, cur));
         RGF_TRY(mm(c, cnt, 1, 0, -1.0f, nullptr, 1, R, cur));  // R = I - M X
         if (s == 1) RGF_CUDA_TRY(cudaMemsetAsync(m->bad_count, 0, sizeof(int), c.st));
-        RGF_TRY(ns_check(cnt, W, c.b, R, p->d_err, p->d_flags, s, steps, cur, nxt, m->bad, m->bad_count, m->theta,
-                         c.st));
+        RGF_TRY(ns_check(cnt, W, c.b, R, c.err, c.flags, s, steps, cur, nxt, m->bad, m->bad_count, m->theta, c.st));
         if (s == 0) RGF_TRY(scale_theta(cnt, c.b, R, m->theta, cur, c.st));
         if (s == 1) {
             RGF_CUDA_TRY(cudaMemcpyAsync(m->h_bad, m->bad_count, sizeof(int), cudaMemcpyDeviceToHost, c.st));
             RGF_CUDA_TRY(cudaStreamSynchronize(c.st));
             if (*m->h_bad > 0) {
-                p->n_reseeds += *m->h_bad;
+                if (c.n_reseeds) *c.n_reseeds += *m->h_bad;
                 RGF_TRY(dfc_to_c128(cnt, c.b, M, m->c128, m->bad, c.st));
                 RGF_TRY(inv_t<double2>(cnt, c.b, m->c128, c.nn, m->inv64_ws, gj_flags, m->bad, c.st));
                 RGF_TRY(c128_to_dfc(cnt, c.b, m->c128, X, m->bad, c.st));
@@ -267,7 +218,6 @@ rgf_status inv_mixed(const Ctx& c, int cnt, int W, const float4* M, float4* X, f
     }
     return RGF_OK;
 }
-}  // namespace
 
 size_t mixed_workspace_bytes(int W, int b) {
     const int Kp = slice_pitch(b);
@@ -280,40 +230,33 @@ size_t mixed_workspace_bytes(int W, int b) {
     return s;
 }
 
-size_t dec_bytes(int W, int b) {
+size_t mixed_dec_bytes(int W, int b) {
     const int Kp = slice_pitch(b);
     return (size_t)kDecUnits * W * b * b * sizeof(double2) + 2 * sa_bytes(2 * W, b, Kp, kSlicesHP) +
-           2 * sb_bytes(2 * W, b, Kp, kSlicesHP) + 1024;
+           2 * sb_bytes(2 * W, b, Kp, kSlicesHP) + (size_t)2 * W * (3 * sizeof(int) + sizeof(double)) + 4096;
 }
 
-rgf_status mixed_init(rgf_plan_s* p) {
-    auto* m = new MixedState();
-    p->mixed = m;
-    m->b = p->b;
-    m->W = p->W;
-    m->Kp = slice_pitch(p->b);
-    const int b = p->b, W = p->W, N = p->N;
+rgf_status mixed_state_init(MixedState* m, int b, int W, void* ws, cudaStream_t st) {
+    m->b = b;
+    m->W = W;
+    m->Kp = slice_pitch(b);
     const size_t nn = (size_t)b * b;
     const char* env = getenv("RGF_OZ_CORE");
     m->core = (env && env[0] == '1') ? 1 : 0;
     auto alloc = [&](void** ptr, size_t bytes) -> rgf_status {
         if (cudaMalloc(ptr, bytes ? bytes : 16) != cudaSuccess) {
             cudaGetLastError();
-            set_error("mixed_init: cudaMalloc(%zu) failed", bytes);
+            set_error("mixed workspace: cudaMalloc(%zu) failed", bytes);
             return RGF_E_OOM;
         }
         return RGF_OK;
     };
-    RGF_TRY(alloc((void**)&m->H_diag, nn * N * sizeof(float4)));
-    RGF_TRY(alloc((void**)&m->S_diag, nn * N * sizeof(float4)));
-    if (N > 1) {
-        RGF_TRY(alloc((void**)&m->H_lower, nn * (N - 1) * sizeof(float4)));
-        RGF_TRY(alloc((void**)&m->S_lower, nn * (N - 1) * sizeof(float4)));
+    if (!ws) {
+        RGF_TRY(alloc(&m->own, mixed_workspace_bytes(W, b)));
+        ws = m->own;
     }
-    for (int s = 0; s < 2; ++s)
-        for (int k = 0; k < 6; ++k) RGF_TRY(alloc((void**)&m->lead[s][k], nn * sizeof(float4)));
     // Carve the workspace.
-    char* w = (char*)p->ws;
+    char* w = (char*)ws;
     m->pool = (float4*)w;
     w += (size_t)kPoolUnits * W * nn * sizeof(float4);
     for (int i = 0; i < 2; ++i) {
@@ -346,13 +289,13 @@ rgf_status mixed_init(rgf_plan_s* p) {
     w = (char*)(((uintptr_t)w + 255) & ~(uintptr_t)255);
     m->colexp = (int*)w;
     // Zero the slice buffers once: the K padding is never written again.
-    RGF_CUDA_TRY(cudaMemsetAsync(m->sa[0], 0, 2 * sa_bytes(2 * W, b, m->Kp) + 2 * sb_bytes(2 * W, b, m->Kp),
-                                 p->stream));
-    RGF_TRY(alloc((void**)&m->status, sizeof(int)));
-    RGF_TRY(alloc((void**)&m->bad_count, sizeof(int)));
+    RGF_CUDA_TRY(cudaMemsetAsync(m->sa[0], 0, 2 * sa_bytes(2 * W, b, m->Kp) + 2 * sb_bytes(2 * W, b, m->Kp), st));
+    RGF_TRY(alloc((void**)&m->status, 2 * sizeof(int)));
+    m->bad_count = m->status + 1;
     {
         char* d = nullptr;
-        RGF_TRY(alloc((void**)&d, dec_bytes(W, b)));
+        RGF_TRY(alloc((void**)&d, mixed_dec_bytes(W, b)));
+        m->dec_own = d;
         m->dec_pool = (double2*)d;
         d += (size_t)kDecUnits * W * nn * sizeof(double2);
         for (int i = 0; i < 2; ++i) {
@@ -363,40 +306,81 @@ rgf_status mixed_init(rgf_plan_s* p) {
             m->hsb[i] = (__nv_bfloat16*)d;
             d += sb_bytes(2 * W, b, m->Kp, kSlicesHP);
         }
+        m->dec_anorm = (double*)d;
+        d += (size_t)2 * W * sizeof(double);
+        m->dec_active = (int*)d;
+        d += (size_t)2 * W * sizeof(int);
+        m->dec_iters = (int*)d;
+        d += (size_t)2 * W * sizeof(int);
+        m->dec_flags = (int*)d;
+        d += (size_t)2 * W * sizeof(int);
+        m->dec_remaining = (int*)d;
         // The K padding of the slice buffers is never written: zero it once.
         RGF_CUDA_TRY(cudaMemsetAsync(m->hsa[0], 0,
                                      2 * sa_bytes(2 * W, b, m->Kp, kSlicesHP) + 2 * sb_bytes(2 * W, b, m->Kp, kSlicesHP),
-                                     p->stream));
+                                     st));
     }
-    if (cudaMallocHost((void**)&m->h_bad, sizeof(int)) != cudaSuccess) {
+    if (cudaMallocHost((void**)&m->h_bad, 2 * sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
-        set_error("mixed_init: cudaMallocHost failed");
+        set_error("mixed workspace: cudaMallocHost failed");
         return RGF_E_OOM;
     }
-    RGF_CUDA_TRY(cudaMemsetAsync(m->status, 0, sizeof(int), p->stream));
-    RGF_CUDA_TRY(cudaStreamSynchronize(p->stream));
+    m->h_remaining = m->h_bad + 1;
+    RGF_CUDA_TRY(cudaMemsetAsync(m->status, 0, 2 * sizeof(int), st));
+    RGF_CUDA_TRY(cudaStreamSynchronize(st));
     return RGF_OK;
 }
 
-void mixed_free(rgf_plan_s* p) {
-    auto* m = (MixedState*)p->mixed;
-    if (!m) return;
-    cudaFree(m->H_diag);
-    cudaFree(m->S_diag);
-    cudaFree(m->H_lower);
-    cudaFree(m->S_lower);
-    for (int s = 0; s < 2; ++s)
-        for (int k = 0; k < 6; ++k) cudaFree(m->lead[s][k]);
+void mixed_state_free(MixedState* m) {
     cudaFree(m->status);
-    cudaFree(m->bad_count);
-    cudaFree(m->dec_pool);
+    cudaFree(m->dec_own);
+    cudaFree(m->own);
     if (m->h_bad) cudaFreeHost(m->h_bad);
-    delete m;
+    m->status = nullptr;
+    m->dec_own = m->own = nullptr;
+    m->h_bad = nullptr;
+}
+
+rgf_status mixed_init(rgf_plan_s* p) {
+    auto* pm = new PlanMixed();
+    p->mixed = pm;
+    const int b = p->b, N = p->N;
+    const size_t nn = (size_t)b * b;
+    auto alloc = [&](void** ptr, size_t bytes) -> rgf_status {
+        if (cudaMalloc(ptr, bytes ? bytes : 16) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("mixed_init: cudaMalloc(%zu) failed", bytes);
+            return RGF_E_OOM;
+        }
+        return RGF_OK;
+    };
+    RGF_TRY(alloc((void**)&pm->H_diag, nn * N * sizeof(float4)));
+    RGF_TRY(alloc((void**)&pm->S_diag, nn * N * sizeof(float4)));
+    if (N > 1) {
+        RGF_TRY(alloc((void**)&pm->H_lower, nn * (N - 1) * sizeof(float4)));
+        RGF_TRY(alloc((void**)&pm->S_lower, nn * (N - 1) * sizeof(float4)));
+    }
+    for (int s = 0; s < 2; ++s)
+        for (int k = 0; k < 6; ++k) RGF_TRY(alloc((void**)&pm->lead[s][k], nn * sizeof(float4)));
+    return mixed_state_init(&pm->ms, b, p->W, p->ws, p->stream);
+}
+
+void mixed_free(rgf_plan_s* p) {
+    auto* pm = (PlanMixed*)p->mixed;
+    if (!pm) return;
+    cudaFree(pm->H_diag);
+    cudaFree(pm->S_diag);
+    cudaFree(pm->H_lower);
+    cudaFree(pm->S_lower);
+    for (int s = 0; s < 2; ++s)
+        for (int k = 0; k < 6; ++k) cudaFree(pm->lead[s][k]);
+    mixed_state_free(&pm->ms);
+    delete pm;
     p->mixed = nullptr;
 }
 
 rgf_status mixed_on_blocks(rgf_plan_s* p) {
-    auto* m = (MixedState*)p->mixed;
+    auto* m = (PlanMixed*)p->mixed;
     const long nn = (long)p->b * p->b;
     RGF_TRY(to_dfc(nn * p->N, p->H_diag, m->H_diag, p->stream));
     RGF_TRY(to_dfc(nn * p->N, p->S_diag, m->S_diag, p->stream));
@@ -409,7 +393,7 @@ rgf_status mixed_on_blocks(rgf_plan_s* p) {
 }
 
 rgf_status mixed_on_lead(rgf_plan_s* p, int side) {
-    auto* m = (MixedState*)p->mixed;
+    auto* m = (PlanMixed*)p->mixed;
     const long nn = (long)p->b * p->b;
     for (int k = 0; k < 6; ++k) RGF_TRY(to_dfc(nn, p->lead[side][k], m->lead[side][k], p->stream));
     RGF_CUDA_TRY(cudaStreamSynchronize(p->stream));
@@ -417,18 +401,18 @@ rgf_status mixed_on_lead(rgf_plan_s* p, int side) {
 }
 
 rgf_status mixed_wave(rgf_plan_s* p, int W) {
-    auto* m = (MixedState*)p->mixed;
+    auto* pm = (PlanMixed*)p->mixed;
+    MixedState* m = &pm->ms;
     cudaStream_t st = p->stream;
     const int b = p->b, N = p->N;
     const long nn = (long)b * b;
     const double eta = p->opt.eta;
     const double* E = p->d_E;
-    Ctx c{m, p, st, nn, b};
+    Ctx c{m, st, nn, b, p->opt.ns_steps, p->d_err, p->d_flags, &p->n_reseeds};
     auto U = [&](int unit) { return m->pool + (long)unit * W * nn; };
     const int W2 = 2 * W;
 
     RGF_CUDA_TRY(cudaMemsetAsync(p->d_flags, 0, sizeof(int) * W, st));
-    RGF_CUDA_TRY(cudaMemsetAsync(p->d_dec_flags, 0, sizeof(int) * W2, st));
     RGF_CUDA_TRY(cudaMemsetAsync(p->d_err, 0, sizeof(double) * W, st));
     RGF_CUDA_TRY(cudaMemsetAsync(m->status, 0, sizeof(int), st));
 
@@ -437,11 +421,22 @@ rgf_status mixed_wave(rgf_plan_s* p, int W) {
     // Sancho-Rubio recursion inverts matrices with condition numbers up to
     // ~1e7 at some energies and needs FP64-class arithmetic there.
     float4 *g = U(8), *t1 = U(14), *t2 = U(16), *t3 = U(18);
-    float4** L = m->lead[0];
-    float4** Rl = m->lead[1];
+    float4** L = pm->lead[0];
+    float4** Rl = pm->lead[1];
     {
+        double2** L64 = p->lead[0];
+        double2** R64 = p->lead[1];
+        auto D = [&](int unit) { return dec_unit(m, W, unit); };
+        FormSrc a{{L64[1], R64[1]}, {L64[0], R64[0]}, {0, 0}};
+        RGF_TRY(form_f64(W, 2, b, E, eta, a, D(2), nullptr, 0.0, nullptr, st));
+        RGF_TRY(copy_f64(W2, b, D(0), D(2), nullptr, st));
+        // Outward coupling: left lead M_{j,j-1} (lower), right lead M_{j,j+1} (upper).
+        FormSrc al{{L64[3], R64[3]}, {L64[2], R64[2]}, {0, 1}};
+        FormSrc be{{L64[3], R64[3]}, {L64[2], R64[2]}, {1, 0}};
+        RGF_TRY(form_f64(W, 2, b, E, eta, al, D(4), nullptr, 0.0, nullptr, st));
+        RGF_TRY(form_f64(W, 2, b, E, eta, be, D(6), nullptr, 0.0, nullptr, st));
         double2* g64 = nullptr;
-        RGF_TRY(hp_decimate(c, W, &g64));
+        RGF_TRY(hp_decimate_run(c, W, p->opt.dec_tol, p->opt.dec_max_iter, &g64));
         RGF_TRY(c128_to_dfc(W2, b, g64, g, nullptr, st));
     }
 
@@ -470,21 +465,21 @@ rgf_status mixed_wave(rgf_plan_s* p, int W) {
     float4 *gi = U(4), *P = U(5), *M = U(6), *Lt = U(7), *Ut = U(8), *Q = U(9), *Qn = U(10);
     float4 *G = U(11), *Xt = U(12), *Yt = U(13), *Rs = U(14);
     if (N == 1) {
-        FormSrcDf a0{{m->S_diag, nullptr}, {m->H_diag, nullptr}, {0, 0}};
+        FormSrcDf a0{{pm->S_diag, nullptr}, {pm->H_diag, nullptr}, {0, 0}};
         RGF_TRY(form_dfc(W, 1, b, E, eta, a0, M, sigL, nullptr, st));
         RGF_TRY(axpy_dfc(W, b, -1.0f, sigR, M, st));
         RGF_TRY(inv_mixed(c, W, W, M, gi, Rs, nullptr, p->d_flags));
         G = gi;
     } else {
-        FormSrcDf a0{{m->S_diag, nullptr}, {m->H_diag, nullptr}, {0, 0}};
+        FormSrcDf a0{{pm->S_diag, nullptr}, {pm->H_diag, nullptr}, {0, 0}};
         RGF_TRY(form_dfc(W, 1, b, E, eta, a0, M, sigL, nullptr, st));
         RGF_TRY(inv_mixed(c, W, W, M, gi, Rs, nullptr, p->d_flags));
         for (int i = 1; i < N; ++i) {
-            const float4* Sl = m->S_lower + (long)(i - 1) * nn;
-            const float4* Hl = m->H_lower + (long)(i - 1) * nn;
+            const float4* Sl = pm->S_lower + (long)(i - 1) * nn;
+            const float4* Hl = pm->H_lower + (long)(i - 1) * nn;
             FormSrcDf up{{Sl, nullptr}, {Hl, nullptr}, {1, 0}};
             FormSrcDf lo{{Sl, nullptr}, {Hl, nullptr}, {0, 0}};
-            FormSrcDf ai{{m->S_diag + (long)i * nn, nullptr}, {m->H_diag + (long)i * nn, nullptr}, {0, 0}};
+            FormSrcDf ai{{pm->S_diag + (long)i * nn, nullptr}, {pm->H_diag + (long)i * nn, nullptr}, {0, 0}};
             RGF_TRY(form_dfc(W, 1, b, E, eta, up, Ut, nullptr, nullptr, st));
             RGF_TRY(form_dfc(W, 1, b, E, eta, lo, Lt, nullptr, nullptr, st));
             RGF_TRY(form_dfc(W, 1, b, E, eta, ai, M, (i == N - 1) ? sigR : nullptr, nullptr, st));

@@ -39,6 +39,29 @@ class rgf_options(ctypes.Structure):
                 ("energy_wave", ctypes.c_int)]
 
 
+class rgf_server_options(ctypes.Structure):
+    _fields_ = [("dec_tol", ctypes.c_double), ("dec_max_iter", ctypes.c_int), ("ns_steps", ctypes.c_int),
+                ("slots", ctypes.c_int), ("class_step", ctypes.c_int), ("capacity_bytes", ctypes.c_size_t)]
+
+
+class rgf_request(ctypes.Structure):
+    _fields_ = [("n_layers", ctypes.c_int), ("b", ctypes.c_int), ("eta", ctypes.c_double),
+                ("H_diag", ctypes.c_void_p), ("S_diag", ctypes.c_void_p), ("H_lower", ctypes.c_void_p),
+                ("S_lower", ctypes.c_void_p), ("lead", (ctypes.c_void_p * 6) * 2), ("E", ctypes.c_void_p),
+                ("n_E", ctypes.c_int), ("mem", ctypes.c_int)]
+
+
+class rgf_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_longlong), ("completed", ctypes.c_longlong),
+                ("rejected", ctypes.c_longlong), ("energies_done", ctypes.c_longlong),
+                ("steps", ctypes.c_longlong), ("decimations", ctypes.c_longlong),
+                ("fp64_reseeds", ctypes.c_longlong), ("engines", ctypes.c_int),
+                ("resident_bytes", ctypes.c_size_t), ("peak_resident_bytes", ctypes.c_size_t),
+                ("workspace_bytes", ctypes.c_size_t), ("busy_s", ctypes.c_double),
+                ("latency_p50_ms", ctypes.c_double), ("latency_p99_ms", ctypes.c_double),
+                ("latency_max_ms", ctypes.c_double)]
+
+
 _lib = None
 _P = ctypes.c_void_p
 _D = ctypes.POINTER(ctypes.c_double)
@@ -78,6 +101,13 @@ def lib():
         "rgf_plan_stats": (ctypes.c_int, [_P] + [ctypes.POINTER(ctypes.c_longlong)] * 2),
         "rgf_gemm_timing": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)]),
+        "rgf_server_options_default": (None, [ctypes.POINTER(rgf_server_options)]),
+        "rgf_server_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(rgf_server_options)]),
+        "rgf_server_submit": (ctypes.c_int, [_P, ctypes.POINTER(rgf_request), ctypes.POINTER(ctypes.c_uint64)]),
+        "rgf_server_poll": (ctypes.c_int, [_P, ctypes.c_uint64, _P, _P, _P, ctypes.POINTER(ctypes.c_double),
+                                           ctypes.c_int]),
+        "rgf_server_stats_get": (ctypes.c_int, [_P, ctypes.POINTER(rgf_server_stats)]),
+        "rgf_server_destroy": (ctypes.c_int, [_P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -292,6 +322,117 @@ def rgf_gemm_timing(enable: bool):
     _check(lib().rgf_gemm_timing(int(bool(enable)), ctypes.byref(ms), ctypes.byref(n), ctypes.byref(fl)),
            "rgf_gemm_timing")
     return ms.value, n.value, fl.value
+
+
+# ----------------------------------------------------------------- server (include/rgf_server.h)
+def rgf_server_options_default() -> rgf_server_options:
+    o = rgf_server_options()
+    lib().rgf_server_options_default(ctypes.byref(o))
+    return o
+
+
+def rgf_server_create(opt: rgf_server_options | None = None):
+    h = _P()
+    _check(lib().rgf_server_create(ctypes.byref(h), ctypes.byref(opt) if opt is not None else None),
+           "rgf_server_create")
+    return h
+
+
+def rgf_server_submit(server, req: rgf_request) -> int:
+    t = ctypes.c_uint64()
+    _check(lib().rgf_server_submit(server, ctypes.byref(req), ctypes.byref(t)), "rgf_server_submit")
+    return t.value
+
+
+def rgf_server_poll(server, ticket: int, T, err=None, flags=None, timeout_us: int = -1):
+    """Returns (status, latency_ms); raises on errors other than not-ready/timeout."""
+    pt, mt = _ptr(T, np.float64)
+    pe, me = _ptr(err, np.float64)
+    pf, mf = _ptr(flags, np.int32)
+    lat = ctypes.c_double(0.0)
+    st = lib().rgf_server_poll(server, int(ticket), pt, pe, pf, ctypes.byref(lat), int(timeout_us))
+    if st in (RGF_E_NOT_READY, RGF_E_TIMEOUT):
+        return st, None
+    _check(st, "rgf_server_poll")
+    return st, lat.value
+
+
+def rgf_server_stats_get(server) -> dict:
+    s = rgf_server_stats()
+    _check(lib().rgf_server_stats_get(server, ctypes.byref(s)), "rgf_server_stats_get")
+    return {name: getattr(s, name) for name, _ in s._fields_}
+
+
+def rgf_server_destroy(server):
+    if server:
+        _check(lib().rgf_server_destroy(server), "rgf_server_destroy")
+
+
+class Server:
+    """Owns one rgf_server_t.  ``submit(dev, E, eta)`` takes a device
+    description (as ``Plan.set_device``) and keeps its arrays alive until the
+    ticket is polled; ``poll`` returns (T, err, flags, latency_ms)."""
+
+    def __init__(self, slots=148, class_step=32, capacity_bytes=0, ns_steps=6, dec_tol=1e-14,
+                 dec_max_iter=100):
+        o = rgf_server_options_default()
+        o.slots, o.class_step, o.capacity_bytes = slots, class_step, capacity_bytes
+        o.ns_steps, o.dec_tol, o.dec_max_iter = ns_steps, dec_tol, dec_max_iter
+        self.handle = rgf_server_create(o)
+        self._keep = {}
+
+    def submit(self, dev, E, eta) -> int:
+        c = lambda a: np.ascontiguousarray(a, dtype=np.complex128)
+        N, b = dev.H_diag.shape[0], dev.H_diag.shape[1]
+        arrs = {"H_diag": c(dev.H_diag), "S_diag": c(dev.S_diag)}
+        if N > 1:
+            arrs["H_lower"], arrs["S_lower"] = c(dev.H_lower), c(dev.S_lower)
+        leads = [[c(getattr(ld, k)) for k in ("H00", "S00", "H10", "S10", "Hc", "Sc")]
+                 for ld in (dev.lead_L, dev.lead_R)]
+        E = np.ascontiguousarray(E, dtype=np.float64)
+        req = rgf_request()
+        req.n_layers, req.b, req.eta, req.n_E, req.mem = N, b, float(eta), E.shape[0], RGF_MEM_HOST
+        for k, a in arrs.items():
+            setattr(req, k, a.ctypes.data)
+        for side in range(2):
+            for k in range(6):
+                req.lead[side][k] = leads[side][k].ctypes.data
+        req.E = E.ctypes.data
+        t = rgf_server_submit(self.handle, req)
+        self._keep[t] = (arrs, leads, E)
+        return t
+
+    def poll(self, ticket, timeout_us=-1):
+        n = self._keep[ticket][2].shape[0]
+        T = np.empty(n)
+        err = np.empty(n)
+        flags = np.empty(n, dtype=np.int32)
+        st, lat = rgf_server_poll(self.handle, ticket, T, err, flags, timeout_us)
+        if st != RGF_OK:
+            return None
+        del self._keep[ticket]
+        return T, err, flags, lat
+
+    def stats(self) -> dict:
+        return rgf_server_stats_get(self.handle)
+
+    def close(self):
+        if self.handle:
+            rgf_server_destroy(self.handle)
+            self.handle = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 # ----------------------------------------------------------------- convenience

@@ -213,3 +213,56 @@ def make_workload(name: str, **override):
     w.update(override)
     dev = make_device(name, **override)
     return dev, energy_grid(w["E_lo"], w["E_hi"], w["n_E"]), float(w["eta"])
+
+
+def uneven_batch(n_dev: int, seed: int, *, N_lo: int, N_hi: int, b_choices, n_E: int,
+                 E_lo: float = -2.0, E_hi: float = 2.0, eta: float = 1e-5,
+                 metal_frac: float = 0.25, gap_offset: float = 0.6):
+    """Devices of uneven length and block size for batched runs.
+
+    Lengths are log-uniform in [N_lo, N_hi] (integers), block sizes drawn
+    uniformly from ``b_choices``, every device a metal-channel-metal junction
+    of the ``junction_N200_b128`` kind with its own seed.  Draw order: the N
+    values, then the b values, then the per-device seeds, all from one
+    ``default_rng(seed)``.  Returns a list of (device, energies, eta).
+    """
+    rng = np.random.default_rng(seed)
+    Ns = np.exp(rng.uniform(math.log(N_lo), math.log(N_hi + 1), n_dev)).astype(np.int64)
+    Ns = np.clip(Ns, max(N_lo, 2), N_hi)
+    bs = rng.choice(np.asarray(b_choices, dtype=np.int64), size=n_dev)
+    seeds = rng.integers(0, 2**31 - 1, size=n_dev)
+    out = []
+    for N, b, s in zip(Ns, bs, seeds):
+        n_metal = int(round(metal_frac * int(N)))
+        mf = metal_frac if 0 < n_metal < int(N) / 2 else 0.0
+        dev = random_device(int(N), int(b), int(s), metal_frac=mf, gap_offset=gap_offset,
+                            name=f"uneven_N{int(N)}_b{int(b)}")
+        out.append((dev, energy_grid(E_lo, E_hi, n_E), float(eta)))
+    return out
+
+
+def serving_trace(seed: int, *, rate: float, duration: float, N_lo: int, N_hi: int, b_lo: int,
+                  b_hi: int, nE_lo: int, nE_hi: int, window: float = 1.5, eta: float = 1e-5):
+    """Poisson arrivals of transport requests.
+
+    Inter-arrival times are exponential with mean 1/rate until ``duration``
+    seconds; each request draws a length log-uniform in [N_lo, N_hi], a block
+    size uniform in [b_lo, b_hi], a number of energies uniform in
+    [nE_lo, nE_hi] and an energy window [c - window, c + window] with its
+    centre c uniform in [-0.5, 0.5].  Returns a list of dicts (t, N, b, n_E,
+    E, eta, seed).  Devices are not drawn here.
+    """
+    rng = np.random.default_rng(seed)
+    out = []
+    t = 0.0
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t >= duration:
+            break
+        N = int(np.clip(np.exp(rng.uniform(math.log(N_lo), math.log(N_hi + 1))), max(N_lo, 2), N_hi))
+        b = int(rng.integers(b_lo, b_hi + 1))
+        n_E = int(rng.integers(nE_lo, nE_hi + 1))
+        c = float(rng.uniform(-0.5, 0.5))
+        out.append(dict(t=t, N=N, b=b, n_E=n_E, E=energy_grid(c - window, c + window, n_E), eta=eta,
+                        seed=int(rng.integers(0, 2**31 - 1))))
+    return out

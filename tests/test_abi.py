@@ -68,3 +68,19 @@ def test_invalid_arguments_fail_before_cuda(L):
     assert L.rgf_set_leads(None, 0, None, None, None, None, None, None, 0) == rgf.RGF_E_INVALID
     assert L.rgf_poll(ctypes.c_uint64(123456789), None, None, None, 0) == rgf.RGF_E_INVALID
     assert L.rgf_plan_destroy(None) == rgf.RGF_OK
+
+
+def test_server_defaults_and_invalid_arguments(L):
+    o = rgf.rgf_server_options_default()
+    assert (o.slots, o.class_step, o.capacity_bytes, o.ns_steps, o.dec_max_iter) == (148, 32, 0, 6, 100)
+    assert o.dec_tol == 1e-14
+    t = ctypes.c_uint64()
+    req = rgf.rgf_request()
+    assert L.rgf_server_submit(None, ctypes.byref(req), ctypes.byref(t)) == rgf.RGF_E_INVALID
+    assert L.rgf_server_create(None, None) == rgf.RGF_E_INVALID
+    bad = rgf.rgf_server_options_default()
+    bad.slots = 0
+    h = ctypes.c_void_p()
+    assert L.rgf_server_create(ctypes.byref(h), ctypes.byref(bad)) == rgf.RGF_E_INVALID
+    assert L.rgf_server_poll(None, 1, None, None, None, None, 0) == rgf.RGF_E_INVALID
+    assert L.rgf_server_destroy(None) == rgf.RGF_OK
