@@ -42,6 +42,12 @@ def parse():
     ap.add_argument("--fp64-wave", type=int, default=16, help="energies of the FP64 GPU comparison step")
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 GPU comparison step")
     ap.add_argument("--cpu-energies", type=int, default=2, help="energies of the oracle CPU sample")
+    ap.add_argument("--batch-devices", type=int, default=64, help="devices of the uneven-batch run")
+    ap.add_argument("--batch-energies", type=int, default=16,
+                    help="energies per device of the uneven-batch run (0 skips it)")
+    ap.add_argument("--serve-seconds", type=float, default=30.0, help="arrival window of the serving run (0 skips it)")
+    ap.add_argument("--serve-rate", type=float, default=1.0, help="Poisson arrival rate of the serving run (1/s)")
+    ap.add_argument("--serve-energies", default="32,128", help="energy-window sizes of serving requests (lo,hi)")
     return ap.parse_args()
 
 
@@ -160,6 +166,86 @@ def run_reference(args, rank, world):
         "e2e": {"value": value, "unit": "energy-points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def run_batched(args, rgf):
+    """Uneven devices through the server: N log-uniform in 50..1000 layers,
+    b in {64, 96, 128, 192, 256, 320}, all submitted at once; energy
+    points per second of wall time from the first submission to the last
+    result.  (Parity of the server against the oracle is in the tests.)"""
+    import numpy as np
+    import torch
+
+    from synth.gpu_devices import random_device_gpu, uneven_shapes
+
+    shapes = uneven_shapes(args.batch_devices, 3, N_lo=50, N_hi=1000, b_choices=[64, 96, 128, 192, 256, 320])
+    devs = [random_device_gpu(N, b, s, metal_frac=0.25, gap_offset=0.6) for N, b, s in shapes]
+    nE = args.batch_energies
+    E = np.linspace(-2.0, 2.0, nE)
+    eta = 1e-5
+    torch.cuda.synchronize()
+    with rgf.Server(slots=148, class_step=32) as sv:
+        t0 = time.perf_counter()
+        tickets = [sv.submit(d, E, eta) for d in devs]
+        res = [sv.poll(t, timeout_us=1_800_000_000) for t in tickets]
+        wall = time.perf_counter() - t0
+        st = sv.stats()
+    if any(r is None for r in res):
+        return {"error": "a request did not complete"}
+    n_pts = nE * len(devs)
+    del devs
+    torch.cuda.empty_cache()
+    Ns = [N for N, _, _ in shapes]
+    return {"workload": "uneven_devices", "devices": len(shapes), "N_range": [min(Ns), max(Ns)],
+            "N_mean": float(np.mean(Ns)), "b_set": sorted({b for _, b, _ in shapes}),
+            "energies_per_device": nE, "eta": eta, "energy_points": n_pts, "seconds": wall,
+            "value": n_pts / wall, "unit": "energy-points/s", "engines": st["engines"], "steps": st["steps"],
+            "decimation_batches": st["decimations"], "fp64_reseeds": st["fp64_reseeds"],
+            "workspace_bytes": st["workspace_bytes"], "peak_resident_bytes": st["peak_resident_bytes"],
+            "flags_nonzero": int(sum(int(np.count_nonzero(r[2] & ~rgf.RGF_FLAG_REFINE)) for r in res)),
+            "max_err_estimate": float(max(float(np.max(r[1])) for r in res))}
+
+
+def run_serving(args, rgf):
+    """Open-loop serving: Poisson arrivals, N log-uniform in 20..2000
+    layers, b uniform in 96..288, energy windows of the given sizes; every
+    request's device is drawn on the GPU before the clock starts and
+    submitted at its arrival time.  Latency = submission to completion."""
+    import numpy as np
+    import torch
+
+    from synth.devices import serving_trace
+    from synth.gpu_devices import random_device_gpu
+
+    lo, hi = (int(x) for x in args.serve_energies.split(","))
+    trace = serving_trace(4, rate=args.serve_rate, duration=args.serve_seconds, N_lo=20, N_hi=2000, b_lo=96,
+                          b_hi=288, nE_lo=lo, nE_hi=hi)
+    devs = [random_device_gpu(r["N"], r["b"], r["seed"], metal_frac=0.25, gap_offset=0.6) for r in trace]
+    torch.cuda.synchronize()
+    with rgf.Server(slots=148, class_step=32) as sv:
+        tickets = []
+        t0 = time.perf_counter()
+        for r, d in zip(trace, devs):
+            delay = t0 + r["t"] - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            tickets.append(sv.submit(d, r["E"], r["eta"]))
+        res = [sv.poll(t, timeout_us=1_800_000_000) for t in tickets]
+        wall = time.perf_counter() - t0
+        st = sv.stats()
+    del devs
+    torch.cuda.empty_cache()
+    ok = [r for r in res if r is not None]
+    n_pts = sum(r["n_E"] for r in trace)
+    work = sum(r["n_E"] * r["N"] * r["b"] ** 3 * 32 for r in trace)  # sweep flop, 32 b^3 per layer
+    return {"workload": "poisson_requests", "rate_per_s": args.serve_rate, "arrival_window_s": args.serve_seconds,
+            "requests": len(trace), "completed": len(ok), "N_range": [20, 2000], "b_range": [96, 288],
+            "energies_per_request": [lo, hi], "energy_points": n_pts, "seconds": wall,
+            "energy_points_per_s": n_pts / wall if wall > 0 else None,
+            "p50_ms": st["latency_p50_ms"], "p99_ms": st["latency_p99_ms"], "max_ms": st["latency_max_ms"],
+            "engines": st["engines"], "peak_resident_bytes": st["peak_resident_bytes"],
+            "capacity_note": "admission capped at min(150 GB, 55% of free device memory)",
+            "offered_sweep_tflop_per_s": work / args.serve_seconds / 1e12 if args.serve_seconds else None}
 
 
 def main():
@@ -336,6 +422,10 @@ def main():
         "flags_first_timed_wave": flag_counts,
         "clocks": clk,
     }
+    if args.batch_energies > 0:
+        line["batched"] = run_batched(args, rgf)
+    if args.serve_seconds > 0:
+        line["serving"] = run_serving(args, rgf)
     print(json.dumps(line), flush=True)
 
 

@@ -296,7 +296,11 @@ rgf_status inv_t(int batch, int b, T2* A, long sA, void* ws, int* flags, const i
         return RGF_E_INVALID;
     }
     if (b < 32) panel = k_gj_panel<T2, 32>;  // nb = b < 32 columns of a 32-lane panel
-    if (smem > 48 * 1024) RGF_CUDA_TRY(cudaFuncSetAttribute(panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (smem > 48 * 1024) {
+        // One fixed limit for every block size: the attribute belongs to the
+        // function, and host threads inverting different sizes share it.
+        RGF_CUDA_TRY(cudaFuncSetAttribute(panel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    }
     const int pitch_nb = (panel == k_gj_panel<T2, 16>) ? 16 : 32;
     for (int k0 = 0; k0 < b; k0 += nb) {
         const int nbk = (b - k0) < nb ? (b - k0) : nb;

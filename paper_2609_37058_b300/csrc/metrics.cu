@@ -13,7 +13,7 @@ namespace rgf {
 namespace {
 std::atomic<unsigned long long> g_launches{0};
 std::mutex g_mu;
-bool g_timing = false;
+std::atomic<bool> g_timing{false};
 struct Rec {
     cudaEvent_t a, b;
     double flops;
@@ -23,7 +23,7 @@ std::vector<Rec> g_recs;
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
-bool gemm_timing_enabled() { return g_timing; }
+bool gemm_timing_enabled() { return g_timing.load(std::memory_order_relaxed); }
 
 void gemm_timing_before(cudaStream_t st, cudaEvent_t* a) {
     cudaEventCreate(a);
@@ -67,7 +67,7 @@ rgf_status rgf_gemm_timing(int enable, double* total_ms, long long* launches, do
         cudaEventDestroy(r.b);
     }
     rgf::g_recs.clear();
-    rgf::g_timing = enable != 0;
+    rgf::g_timing.store(enable != 0);
     return RGF_OK;
 }
 

@@ -2,6 +2,7 @@
 // legacy-path reference core of the slice-product complex GEMM, and the
 // double-float elementwise steps (block formation, decimation updates,
 // broadenings, Newton-Schulz bookkeeping, the FP64 trace reduction).
+#include <atomic>
 #include "df.cuh"
 #include "mixed.h"
 
@@ -285,10 +286,10 @@ __global__ void __launch_bounds__(256) k_oz_mma(OzGemm g) {
 rgf_status oz_gemm_mma(const OzGemm& g, cudaStream_t st) {
     if (g.batch <= 0) return RGF_OK;
     const size_t smem = 2ull * kSlices * MM_BM * MM_PITCH * sizeof(__nv_bfloat16);
-    static bool attr = false;
-    if (!attr) {
+    static std::atomic<bool> attr{false};
+    if (!attr.load()) {
         RGF_CUDA_TRY(cudaFuncSetAttribute(k_oz_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr = true;
+        attr.store(true);
     }
     dim3 grid(ceil_div(2L * g.n, MM_BN), ceil_div(g.m, MM_BM), g.batch);
     k_oz_mma<<<grid, 256, smem, st>>>(g);

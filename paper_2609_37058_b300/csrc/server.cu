@@ -781,14 +781,18 @@ rgf_status rgf_server_destroy(rgf_server_t h) {
     cudaDeviceSynchronize();
     for (auto& kv : sv->tickets) {
         Request* r = kv.second;
-        cudaFree(r->blk);
-        cudaFree(r->lead);
-        cudaFree(r->out);
+        if (r->blk) cudaFreeAsync(r->blk, sv->io_st);
+        if (r->lead) cudaFreeAsync(r->lead, sv->io_st);
+        if (r->out) cudaFreeAsync(r->out, sv->io_st);
         if (r->ready_ev) cudaEventDestroy(r->ready_ev);
         delete r;
     }
+    cudaStreamSynchronize(sv->io_st);
     for (auto& kv : sv->engines) rgf::engine_free(kv.second.get());
     cudaFree(sv->staging);
+    // Hand the request memory cached in the stream-ordered pool back.
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, sv->device) == cudaSuccess) cudaMemPoolTrimTo(pool, 0);
     cudaStreamDestroy(sv->upload_st);
     cudaStreamDestroy(sv->io_st);
     cudaGetLastError();

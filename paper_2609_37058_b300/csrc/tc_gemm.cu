@@ -14,6 +14,7 @@
 //     (sign, addend, identity) and store float4 (re_hi, re_lo, im_hi, im_lo).
 // Every wait on an mbarrier is bounded (2 s); a timeout sets a status bit
 // that the host turns into an error, and the CTA still releases its TMEM.
+#include <atomic>
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -324,15 +325,17 @@ __global__ void __launch_bounds__(128, 1)
 // The driver's tensor-map encoder, looked up at run time so that the library
 // loads (and its host-only entry points work) on machines without a driver.
 static PFN_cuTensorMapEncodeTiled_v12000 encoder() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    if (!fn) {
+    // Initialised once, thread-safely, on first use.
+    static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
         void* p = nullptr;
         cudaDriverEntryPointQueryResult q;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
                 cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
-            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-    }
+            return (PFN_cuTensorMapEncodeTiled_v12000)p;
+        cudaGetLastError();
+        return (PFN_cuTensorMapEncodeTiled_v12000) nullptr;
+    }();
     return fn;
 }
 
@@ -372,11 +375,12 @@ static rgf_status launch_tc(const TcArgs& g, cudaStream_t st) {
     CUtensorMap ta, tb;
     RGF_TRY(encode_slices(&ta, g.As, g.Kp, g.m, (long)g.batch * NSL, TC_BM));
     RGF_TRY(encode_slices(&tb, g.Bs, g.Kp, 2L * g.n, (long)g.batch * NSL, BN));
-    static bool attr = false;
-    if (!attr) {
+    static std::atomic<bool> attr{false};
+    if (!attr.load()) {
+        // Idempotent: threads that race here all set the same value.
         RGF_CUDA_TRY(cudaFuncSetAttribute(k_oz_tc<NSL, NGRP, BN, OUT64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           Cfg::SMEM));
-        attr = true;
+        attr.store(true);
     }
     dim3 grid(ceil_div(2L * g.n, BN), ceil_div(g.m, TC_BM), g.batch);
     // Only unmasked launches are timed: their work is exactly known.

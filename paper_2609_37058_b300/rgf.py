@@ -382,28 +382,48 @@ class Server:
         self._keep = {}
 
     def submit(self, dev, E, eta) -> int:
-        c = lambda a: np.ascontiguousarray(a, dtype=np.complex128)
-        N, b = dev.H_diag.shape[0], dev.H_diag.shape[1]
-        arrs = {"H_diag": c(dev.H_diag), "S_diag": c(dev.S_diag)}
-        if N > 1:
-            arrs["H_lower"], arrs["S_lower"] = c(dev.H_lower), c(dev.S_lower)
-        leads = [[c(getattr(ld, k)) for k in ("H00", "S00", "H10", "S10", "Hc", "Sc")]
-                 for ld in (dev.lead_L, dev.lead_R)]
-        E = np.ascontiguousarray(E, dtype=np.float64)
+        """Queue one device.  Host devices (numpy arrays) are read from host
+        memory; devices whose arrays are CUDA tensors (synth.gpu_devices) are
+        read in place from device memory (synchronise their producer first)."""
+        N, b = int(dev.H_diag.shape[0]), int(dev.H_diag.shape[1])
+        on_gpu = hasattr(dev.H_diag, "data_ptr")
+        if on_gpu:
+            import torch
+            chk = lambda t: t if (t.is_cuda and t.dtype == torch.complex128 and t.is_contiguous()) else None
+            arrs = {"H_diag": chk(dev.H_diag), "S_diag": chk(dev.S_diag)}
+            if N > 1:
+                arrs["H_lower"], arrs["S_lower"] = chk(dev.H_lower), chk(dev.S_lower)
+            leads = [[chk(t) for t in L] for L in (dev.lead_L, dev.lead_R)]
+            if any(v is None for v in arrs.values()) or any(v is None for L in leads for v in L):
+                raise TypeError("device arrays must be contiguous complex128 CUDA tensors")
+            E = torch.as_tensor(np.asarray(E, dtype=np.float64)).to("cuda")
+            ptr = lambda t: t.data_ptr()
+            n_E, mem = int(E.shape[0]), RGF_MEM_DEVICE
+            torch.cuda.synchronize()
+        else:
+            c = lambda a: np.ascontiguousarray(a, dtype=np.complex128)
+            arrs = {"H_diag": c(dev.H_diag), "S_diag": c(dev.S_diag)}
+            if N > 1:
+                arrs["H_lower"], arrs["S_lower"] = c(dev.H_lower), c(dev.S_lower)
+            leads = [[c(getattr(ld, k)) for k in ("H00", "S00", "H10", "S10", "Hc", "Sc")]
+                     for ld in (dev.lead_L, dev.lead_R)]
+            E = np.ascontiguousarray(E, dtype=np.float64)
+            ptr = lambda a: a.ctypes.data
+            n_E, mem = int(E.shape[0]), RGF_MEM_HOST
         req = rgf_request()
-        req.n_layers, req.b, req.eta, req.n_E, req.mem = N, b, float(eta), E.shape[0], RGF_MEM_HOST
+        req.n_layers, req.b, req.eta, req.n_E, req.mem = N, b, float(eta), n_E, mem
         for k, a in arrs.items():
-            setattr(req, k, a.ctypes.data)
+            setattr(req, k, ptr(a))
         for side in range(2):
             for k in range(6):
-                req.lead[side][k] = leads[side][k].ctypes.data
-        req.E = E.ctypes.data
+                req.lead[side][k] = ptr(leads[side][k])
+        req.E = ptr(E)
         t = rgf_server_submit(self.handle, req)
-        self._keep[t] = (arrs, leads, E)
+        self._keep[t] = (arrs, leads, E, n_E)
         return t
 
     def poll(self, ticket, timeout_us=-1):
-        n = self._keep[ticket][2].shape[0]
+        n = self._keep[ticket][3]
         T = np.empty(n)
         err = np.empty(n)
         flags = np.empty(n, dtype=np.int32)

@@ -106,3 +106,14 @@ def test_poll_timeout_and_not_ready(rgf):
         if r is None:
             r = sv.poll(t, timeout_us=300_000_000)
         assert r is not None and np.all(np.isfinite(r[0]))
+
+
+def test_concurrent_engines_with_large_blocks(rgf):
+    # Several block-size engines whose inverses need more than 48 KB of
+    # shared memory run at the same time on their own host threads.
+    jobs = [(random_device(3, b, 40 + i), energy_grid(-1.0, 1.0, 6), 1e-5)
+            for i, b in enumerate([192, 224, 256, 160, 200])]
+    res, stats = serve(rgf, jobs, slots=8, class_step=32)
+    assert stats["engines"] == 4
+    for (dev, E, eta), (T, err, flags, lat) in zip(jobs, res):
+        assert np.abs(T - o.transmission(dev, E, eta)).max() <= MIXED_ABS, dev.b
