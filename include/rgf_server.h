@@ -94,6 +94,15 @@ void rgf_server_options_default(rgf_server_options* opt);
 /* Create a server on the current CUDA device.  opt may be NULL. */
 rgf_status rgf_server_create(rgf_server_t* server, const rgf_server_options* opt);
 
+/* Per-class settings, normally from the autotuner
+ * (paper_2609_37058_b300/autotune.py): for requests whose padded block size
+ * is block_class, use `slots` energy slots (0 = the server default), tile_n
+ * real output columns per tensor-core CTA (64, 80 or 96; 0 = 96) and a
+ * Gauss-Jordan panel width of `panel` columns for the FP32 seed inverse
+ * (16 or 32; 0 = default).  Must precede the first request of that class
+ * (RGF_E_STATE otherwise); RGF_E_INVALID for values out of range. */
+rgf_status rgf_server_set_class(rgf_server_t server, int block_class, int slots, int tile_n, int panel);
+
 /* Queue a request; returns at once with a ticket.  RGF_E_INVALID for bad
  * sizes or pointers, RGF_E_REJECTED if its resident bytes exceed the
  * capacity on their own. */

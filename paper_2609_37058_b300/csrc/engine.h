@@ -17,8 +17,8 @@ struct SlotTab {
     double* outT;       // where the item's results go (set on its last layer)
     double* outErr;
     int* outFlags;
-    int ready;          // index in the ready buffer when the slot is refilled now, else -1
-    int pad_;
+    int ready;          // index in the ready buffer when the slot is refilled now
+    int ready_D;        // items of the decimation batch that filled the ready buffer
 };
 
 // Masks that accompany a table of S slots (each an int[S] array).
@@ -43,10 +43,11 @@ rgf_status pad_to_dfc(int nblk, int b, int bc, const double2* src, float4* dst, 
 rgf_status pad_f64(int nblk, int b, int bc, const double2* src, double2* dst, double diag_fill, cudaStream_t st);
 
 // Refilled slots: copy the item's Sigma_L, Sigma_R, Gamma_L, Gamma_R (ready
-// buffer, entries r, D + r for Sigma and 2D + r, 3D + r for Gamma) into the
-// slot store (entries s, S + s, 2S + s, 3S + s) and reset err/flags from the
-// item's decimation results.
-rgf_status engine_refill(int S, int D, int bc, const SlotTab* tab, const int* refill, const float4* ready,
+// buffer, entries r, D + r for Sigma and 2D + r, 3D + r for Gamma, with
+// r = tab[s].ready and D = tab[s].ready_D) into the slot store (entries s,
+// S + s, 2S + s, 3S + s) and reset err/flags from the item's decimation
+// results.
+rgf_status engine_refill(int S, int bc, const SlotTab* tab, const int* refill, const float4* ready,
                          float4* store, const double* dec_err, const int* dec_flags, double* slot_err,
                          int* slot_flags, cudaStream_t st);
 // M = z S_ll - H_ll - [first] Sigma_L - [last] Sigma_R for active slots;

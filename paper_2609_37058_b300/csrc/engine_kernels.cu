@@ -49,12 +49,12 @@ __global__ void k_pad_f64(int b, int bc, const double2* __restrict__ src, double
     }
 }
 
-__global__ void k_refill(int S, int D, int bc, const SlotTab* __restrict__ tab, const int* __restrict__ refill,
+__global__ void k_refill(int S, int bc, const SlotTab* __restrict__ tab, const int* __restrict__ refill,
                          const float4* __restrict__ ready, float4* __restrict__ store, const double* dec_err,
                          const int* dec_flags, double* slot_err, int* slot_flags) {
     const int s = blockIdx.y;
     if (!refill[s]) return;
-    const int r = tab[s].ready;
+    const int r = tab[s].ready, D = tab[s].ready_D;
     const long nn = (long)bc * bc;
     for (int k = 0; k < 4; ++k) {
         const float4* src = ready + ((long)k * D + r) * nn;
@@ -212,10 +212,10 @@ rgf_status pad_f64(int nblk, int b, int bc, const double2* src, double2* dst, do
     return RGF_OK;
 }
 
-rgf_status engine_refill(int S, int D, int bc, const SlotTab* tab, const int* refill, const float4* ready,
+rgf_status engine_refill(int S, int bc, const SlotTab* tab, const int* refill, const float4* ready,
                          float4* store, const double* dec_err, const int* dec_flags, double* slot_err,
                          int* slot_flags, cudaStream_t st) {
-    k_refill<<<dim3(chunks((long)bc * bc, 256, 32), S), 256, 0, st>>>(S, D, bc, tab, refill, ready, store, dec_err,
+    k_refill<<<dim3(chunks((long)bc * bc, 256, 32), S), 256, 0, st>>>(S, bc, tab, refill, ready, store, dec_err,
                                                                       dec_flags, slot_err, slot_flags);
     RGF_LAUNCH_CHECK();
     return RGF_OK;

@@ -3,6 +3,8 @@
 // for the FP32 seed inverse of the mixed path).
 #pragma once
 
+#include <atomic>
+
 #include "kernels.h"
 
 namespace rgf {
@@ -278,10 +280,15 @@ __global__ void __launch_bounds__(256) k_gj_unpermute(int b, T2* A, long sA, con
     }
 }
 
+// nb_override (16, or 32 where that is the default) replaces the default
+// panel width for b >= 64; 0 keeps it.  The workspace is sized for the
+// default, which is never narrower.
 template <typename T2>
-rgf_status inv_t(int batch, int b, T2* A, long sA, void* ws, int* flags, const int* active, cudaStream_t st) {
+rgf_status inv_t(int batch, int b, T2* A, long sA, void* ws, int* flags, const int* active, cudaStream_t st,
+                 int nb_override = 0) {
     if (batch <= 0) return RGF_OK;
-    const int nb = gj_nb(b);
+    int nb = gj_nb(b);
+    if (b >= 64 && (nb_override == 16 || (nb_override == 32 && nb == 32))) nb = nb_override;
     T2* Pbar = (T2*)ws;
     T2* T = Pbar + (size_t)batch * b * nb;
     int* piv = (int*)(T + (size_t)batch * b * nb);
@@ -297,9 +304,16 @@ rgf_status inv_t(int batch, int b, T2* A, long sA, void* ws, int* flags, const i
     }
     if (b < 32) panel = k_gj_panel<T2, 32>;  // nb = b < 32 columns of a 32-lane panel
     if (smem > 48 * 1024) {
-        // One fixed limit for every block size: the attribute belongs to the
-        // function, and host threads inverting different sizes share it.
-        RGF_CUDA_TRY(cudaFuncSetAttribute(panel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        // One fixed limit for every block size, set once per panel width:
+        // the attribute belongs to the function, and host threads inverting
+        // different sizes share it.  (Set once, it is not repeated inside a
+        // stream capture.)
+        static std::atomic<bool> done[2] = {false, false};
+        std::atomic<bool>& d = done[panel == k_gj_panel<T2, 16> ? 1 : 0];
+        if (!d.load()) {
+            RGF_CUDA_TRY(cudaFuncSetAttribute(panel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+            d.store(true);
+        }
     }
     const int pitch_nb = (panel == k_gj_panel<T2, 16>) ? 16 : 32;
     for (int k0 = 0; k0 < b; k0 += nb) {

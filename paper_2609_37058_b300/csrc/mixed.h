@@ -67,6 +67,8 @@ struct OzGemm {
     // loads of the first K chunk and use this wait limit in nanoseconds, so
     // that its bounded waits run out and report through *status.
     unsigned long long test_wait_ns;
+    // Real output columns per CTA of the tcgen05 core: 64, 80 or 96 (0 = 96).
+    int bn;
 };
 
 struct OzGemmHP {
@@ -143,6 +145,8 @@ rgf_status dfc_to_c128(int batch, int b, const float4* X, double2* Y, const int*
 rgf_status c128_to_dfc(int batch, int b, const double2* X, float4* Y, const int* mask, cudaStream_t st);
 // out[i] = act ? act[i] : 1
 rgf_status mask_init(int batch, const int* act, int* out, cudaStream_t st);
+// *acc += *count (one thread)
+rgf_status accumulate_count(long long* acc, const int* count, cudaStream_t st);
 rgf_status ns_check_f64(int batch, int W, int b, const double2* R, double* err, int* flags, int step, int max_steps,
                         const int* act, int* next_act, int* bad, int* bad_count, cudaStream_t st);
 rgf_status c128_to_c64(int batch, int b, const double2* X, float2* Y, const int* mask, cudaStream_t st);

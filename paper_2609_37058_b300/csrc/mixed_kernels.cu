@@ -760,6 +760,14 @@ rgf_status mask_init(int batch, const int* act, int* out, cudaStream_t st) {
     return RGF_OK;
 }
 
+__global__ void k_accumulate_count(long long* acc, const int* count) { *acc += *count; }
+
+rgf_status accumulate_count(long long* acc, const int* count, cudaStream_t st) {
+    k_accumulate_count<<<1, 1, 0, st>>>(acc, count);
+    RGF_LAUNCH_CHECK();
+    return RGF_OK;
+}
+
 __global__ void k_trace_dfc(int b, const float4* X, const float4* Y, double* T, double* Ti) {
     __shared__ double sh[32];
     const long nn = (long)b * b, off = (long)blockIdx.x * nn;

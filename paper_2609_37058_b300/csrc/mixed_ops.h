@@ -20,6 +20,7 @@ struct MixedState {
     float2* c64 = nullptr;
     void* inv_ws = nullptr;
     int* status = nullptr;   // tcgen05 pipeline timeout word
+    long long* reseed_acc = nullptr;  // FP64 reseeds counted on the device (graph mode)
     int* nsact[2] = {};
     int* bad = nullptr;
     int* bad_count = nullptr;
@@ -39,6 +40,8 @@ struct MixedState {
     int* dec_remaining = nullptr;
     int* h_remaining = nullptr;  // pinned
     int core = 0;                // 0 = tcgen05, 1 = mma.sync reference core
+    int bn = 96;                 // tcgen05 tile width of the double-float GEMM (64, 80, 96)
+    int gj_nb = 0;               // panel width of the FP32 seed inverse (0 = default, 16 or 32)
     void* own = nullptr;         // allocation owned by the state (when ws was not given)
     void* dec_own = nullptr;
 };
@@ -63,6 +66,10 @@ struct Ctx {
     double* err;           // per energy (entry i -> energy i mod W)
     int* flags;            // per energy
     long long* n_reseeds;  // host counter
+    // Graph mode: no host synchronisation inside; the FP64 reseed path is
+    // always launched, masked by the entries that need it, and reseeds are
+    // counted in MixedState::reseed_acc.
+    bool graph = false;
 };
 
 // Slice A by rows into sa[ia], B by columns into sb[ib]; C = alpha A B (+ D) (+ I).

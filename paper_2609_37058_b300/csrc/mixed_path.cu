@@ -57,6 +57,7 @@ rgf_status mm(const Ctx& c, int cnt, int ia, int ib, float alpha, const float4* 
     g.sC = c.nn;
     g.active = act;
     g.status = c.m->status;
+    g.bn = c.m->bn;
     return oz_gemm(g, c.m->core, c.st);
 }
 
@@ -185,7 +186,7 @@ rgf_status inv_mixed(const Ctx& c, int cnt, int W, const float4* M, float4* X, f
     RGF_TRY(dfc_hi_to_c64(cnt, c.b, M, m->c64, act, c.st));
     // An FP32 seed with a zero pivot is not reported: its residual is not
     // finite, so it is reseeded in FP64 below, which reports its own pivots.
-    RGF_TRY(inv_t<float2>(cnt, c.b, m->c64, c.nn, m->inv_ws, nullptr, act, c.st));
+    RGF_TRY(inv_t<float2>(cnt, c.b, m->c64, c.nn, m->inv_ws, nullptr, act, c.st, m->gj_nb));
     RGF_TRY(c64_to_dfc(cnt, c.b, m->c64, X, act, c.st));
     const int steps = c.ns_steps;
     if (steps == 0) return RGF_OK;
@@ -199,7 +200,14 @@ rgf_status inv_mixed(const Ctx& c, int cnt, int W, const float4* M, float4* X, f
         if (s == 1) RGF_CUDA_TRY(cudaMemsetAsync(m->bad_count, 0, sizeof(int), c.st));
         RGF_TRY(ns_check(cnt, W, c.b, R, c.err, c.flags, s, steps, cur, nxt, m->bad, m->bad_count, m->theta, c.st));
         if (s == 0) RGF_TRY(scale_theta(cnt, c.b, R, m->theta, cur, c.st));
-        if (s == 1) {
+        if (s == 1 && c.graph) {
+            RGF_TRY(accumulate_count(m->reseed_acc, m->bad_count, c.st));
+            RGF_TRY(dfc_to_c128(cnt, c.b, M, m->c128, m->bad, c.st));
+            RGF_TRY(inv_t<double2>(cnt, c.b, m->c128, c.nn, m->inv64_ws, gj_flags, m->bad, c.st));
+            RGF_TRY(c128_to_dfc(cnt, c.b, m->c128, X, m->bad, c.st));
+            RGF_TRY(sliceB(c, cnt, 0, X, m->bad));
+            RGF_TRY(mm(c, cnt, 1, 0, -1.0f, nullptr, 1, R, m->bad));
+        } else if (s == 1) {
             RGF_CUDA_TRY(cudaMemcpyAsync(m->h_bad, m->bad_count, sizeof(int), cudaMemcpyDeviceToHost, c.st));
             RGF_CUDA_TRY(cudaStreamSynchronize(c.st));
             if (*m->h_bad > 0) {
@@ -290,8 +298,9 @@ rgf_status mixed_state_init(MixedState* m, int b, int W, void* ws, cudaStream_t 
     m->colexp = (int*)w;
     // Zero the slice buffers once: the K padding is never written again.
     RGF_CUDA_TRY(cudaMemsetAsync(m->sa[0], 0, 2 * sa_bytes(2 * W, b, m->Kp) + 2 * sb_bytes(2 * W, b, m->Kp), st));
-    RGF_TRY(alloc((void**)&m->status, 2 * sizeof(int)));
+    RGF_TRY(alloc((void**)&m->status, 4 * sizeof(int)));
     m->bad_count = m->status + 1;
+    m->reseed_acc = (long long*)(m->status + 2);
     {
         char* d = nullptr;
         RGF_TRY(alloc((void**)&d, mixed_dec_bytes(W, b)));
@@ -326,7 +335,7 @@ rgf_status mixed_state_init(MixedState* m, int b, int W, void* ws, cudaStream_t 
         return RGF_E_OOM;
     }
     m->h_remaining = m->h_bad + 1;
-    RGF_CUDA_TRY(cudaMemsetAsync(m->status, 0, 2 * sizeof(int), st));
+    RGF_CUDA_TRY(cudaMemsetAsync(m->status, 0, 4 * sizeof(int), st));
     RGF_CUDA_TRY(cudaStreamSynchronize(st));
     return RGF_OK;
 }

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <string>
 #include <condition_variable>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -83,7 +84,9 @@ struct Engine {
     SlotTab* h_tab = nullptr;  // pinned
     int* h_masks = nullptr;    // pinned
     DecTab* h_dtab = nullptr;  // pinned
-    float4 *Q = nullptr, *Qn = nullptr;
+    bool graphs = true;             // replay each step as a CUDA graph
+    cudaGraphExec_t gx[2] = {};     // one per Q/Qn parity
+    int parity = 0;                 // 0: Q = unit 9, 1: Q = unit 10
     std::atomic<long long> steps{0}, decs{0};
     long long reseeds = 0;  // engine thread; copied to reseeds_seen after each step
     std::atomic<long long> reseeds_seen{0};
@@ -93,8 +96,13 @@ struct Engine {
     float4* U(int u) const { return ms.pool + (long)u * W * bc * bc; }
 };
 
+struct ClassCfg {
+    int slots = 0, tile_n = 0, panel = 0;
+};
+
 struct Server {
     rgf_server_options opt{};
+    std::map<int, ClassCfg> class_cfg;  // guarded by mu
     int device = 0;
     std::mutex mu;
     std::condition_variable cv_admit;  // queue or resident bytes changed
@@ -151,8 +159,8 @@ rgf_status engine_init(Engine* e) {
     RGF_CUDA_TRY(cudaMallocHost((void**)&e->h_masks, sizeof(int) * 5 * W));
     RGF_CUDA_TRY(cudaMallocHost((void**)&e->h_dtab, sizeof(DecTab) * W));
     e->slots.assign(W, Engine::Slot{});
-    e->Q = e->U(9);
-    e->Qn = e->U(10);
+    const char* ng = getenv("RGF_NO_GRAPHS");
+    e->graphs = !(ng && ng[0] == '1');
     (void)sv;
     return RGF_OK;
 }
@@ -169,6 +177,8 @@ void engine_free(Engine* e) {
     if (e->h_tab) cudaFreeHost(e->h_tab);
     if (e->h_masks) cudaFreeHost(e->h_masks);
     if (e->h_dtab) cudaFreeHost(e->h_dtab);
+    for (auto& g : e->gx)
+        if (g) cudaGraphExecDestroy(g);
     mixed_state_free(&e->ms);
     if (e->st) cudaStreamDestroy(e->st);
 }
@@ -237,10 +247,64 @@ rgf_status engine_decimate(Engine* e, const std::vector<std::pair<Request*, int>
     return RGF_OK;
 }
 
-// One layer for every active slot.
-rgf_status engine_step(Engine* e) {
+// Kernels of one layer for every active slot.  With all = true every kernel
+// is launched (masks select the entries) so that the sequence is the same
+// every step and can be captured as a graph; Q/Qn are the buffers of the
+// given parity.
+rgf_status engine_issue(Engine* e, bool all, int n_nf, int n_first, int n_last, int n_refill, float4* Q,
+                        float4* Qn) {
     const int W = e->W, bc = e->bc;
     cudaStream_t st = e->st;
+    RGF_CUDA_TRY(cudaMemcpyAsync(e->d_tab, e->h_tab, sizeof(SlotTab) * W, cudaMemcpyHostToDevice, st));
+    RGF_CUDA_TRY(cudaMemcpyAsync(e->d_masks, e->h_masks, sizeof(int) * 5 * W, cudaMemcpyHostToDevice, st));
+    const int* d_act = e->d_masks;
+    const int* d_nf = d_act + W;
+    const int* d_first = d_act + 2 * W;
+    const int* d_last = d_act + 3 * W;
+    const int* d_refill = d_act + 4 * W;
+    if (all || n_refill)
+        RGF_TRY(engine_refill(W, bc, e->d_tab, d_refill, e->U(16), e->U(0), e->dec_err, e->dec_flags, e->slot_err,
+                              e->slot_flags, st));
+    float4 *sigL = e->U(0), *sigR = e->U(1), *gamL = e->U(2), *gamR = e->U(3);
+    float4 *gi = e->U(4), *P = e->U(5), *M = e->U(6), *Lt = e->U(7), *Ut = e->U(8);
+    float4 *G = e->U(11), *Xt = e->U(12), *Yt = e->U(13), *Rs = e->U(14);
+    SlotMasks mk{d_act, d_nf, d_first, d_last, d_refill};
+    RGF_TRY(engine_form_step(W, bc, e->d_tab, mk, sigL, sigR, M, Ut, Lt, st));
+    Ctx c = engine_ctx(e, e->slot_err, e->slot_flags);
+    c.graph = all;
+    if (all || n_nf) {
+        RGF_TRY(sliceA(c, W, 0, gi, d_nf));
+        RGF_TRY(sliceB(c, W, 0, Ut, d_nf));
+        RGF_TRY(mm(c, W, 0, 0, -1.0f, nullptr, 0, P, d_nf));  // P = -g tau'
+        RGF_TRY(sliceA(c, W, 0, Lt, d_nf));
+        RGF_TRY(sliceB(c, W, 0, P, d_nf));
+        RGF_TRY(mm(c, W, 0, 0, 1.0f, M, 0, M, d_nf));  // M += tau P
+        RGF_TRY(sliceA(c, W, 1, Q, d_nf));
+        RGF_TRY(mm(c, W, 1, 0, 1.0f, nullptr, 0, Qn, d_nf));  // Q P, the next step's Q
+    }
+    // Slots on their first layer start the chain with Q = I in the next
+    // step's Q buffer.
+    if (all || n_first) RGF_TRY(set_identity_masked_dfc(W, bc, Qn, d_first, st));
+    RGF_TRY(inv_mixed(c, W, W, M, gi, Rs, d_act, e->slot_flags));
+    if (all || n_last) {
+        RGF_TRY(sliceA(c, W, 0, Qn, d_last));
+        RGF_TRY(sliceB(c, W, 0, gi, d_last));
+        RGF_TRY(mm(c, W, 0, 0, 1.0f, nullptr, 0, G, d_last));  // G_{0,N-1} = Q g
+        RGF_TRY(sliceA(c, W, 0, gamL, d_last));
+        RGF_TRY(sliceB(c, W, 0, G, d_last));
+        RGF_TRY(mm(c, W, 0, 0, 1.0f, nullptr, 0, Xt, d_last));
+        RGF_TRY(sliceA(c, W, 0, G, d_last));
+        RGF_TRY(sliceB(c, W, 0, gamR, d_last));
+        RGF_TRY(mm(c, W, 0, 0, 1.0f, nullptr, 0, Yt, d_last));
+        RGF_TRY(trace_masked_dfc(W, bc, Xt, Yt, d_last, e->slot_T, st));
+        RGF_TRY(engine_finish(W, e->d_tab, d_last, e->slot_T, e->slot_err, e->slot_flags, st));
+    }
+    return RGF_OK;
+}
+
+// One layer for every active slot.
+rgf_status engine_step(Engine* e) {
+    const int W = e->W;
     int* act = e->h_masks;
     int* nf = act + W;
     int* first = act + 2 * W;
@@ -275,52 +339,44 @@ rgf_status engine_step(Engine* e) {
         t.outErr = r->Err() + sl.k;
         t.outFlags = r->Flags() + sl.k;
     }
-    RGF_CUDA_TRY(cudaMemcpyAsync(e->d_tab, e->h_tab, sizeof(SlotTab) * W, cudaMemcpyHostToDevice, st));
-    RGF_CUDA_TRY(cudaMemcpyAsync(e->d_masks, e->h_masks, sizeof(int) * 5 * W, cudaMemcpyHostToDevice, st));
+    cudaStream_t st = e->st;
     RGF_CUDA_TRY(cudaMemsetAsync(e->ms.status, 0, sizeof(int), st));
-    const int* d_act = e->d_masks;
-    const int* d_nf = d_act + W;
-    const int* d_first = d_act + 2 * W;
-    const int* d_last = d_act + 3 * W;
-    const int* d_refill = d_act + 4 * W;
-    if (n_refill)
-        RGF_TRY(engine_refill(W, e->ready_D, bc, e->d_tab, d_refill, e->U(16), e->U(0), e->dec_err, e->dec_flags,
-                              e->slot_err, e->slot_flags, st));
-    float4 *sigL = e->U(0), *sigR = e->U(1), *gamL = e->U(2), *gamR = e->U(3);
-    float4 *gi = e->U(4), *P = e->U(5), *M = e->U(6), *Lt = e->U(7), *Ut = e->U(8);
-    float4 *G = e->U(11), *Xt = e->U(12), *Yt = e->U(13), *Rs = e->U(14);
-    SlotMasks mk{d_act, d_nf, d_first, d_last, d_refill};
-    RGF_TRY(engine_form_step(W, bc, e->d_tab, mk, sigL, sigR, M, Ut, Lt, st));
-    Ctx c = engine_ctx(e, e->slot_err, e->slot_flags);
-    if (n_nf) {
-        RGF_TRY(sliceA(c, W, 0, gi, d_nf));
-        RGF_TRY(sliceB(c, W, 0, Ut, d_nf));
-        RGF_TRY(mm(c, W, 0, 0, -1.0f, nullptr, 0, P, d_nf));  // P = -g tau'
-        RGF_TRY(sliceA(c, W, 0, Lt, d_nf));
-        RGF_TRY(sliceB(c, W, 0, P, d_nf));
-        RGF_TRY(mm(c, W, 0, 0, 1.0f, M, 0, M, d_nf));  // M += tau P
-        RGF_TRY(sliceA(c, W, 1, e->Q, d_nf));
-        RGF_TRY(mm(c, W, 1, 0, 1.0f, nullptr, 0, e->Qn, d_nf));  // Q P
-        std::swap(e->Q, e->Qn);
+    float4* Q = e->U(9 + e->parity);
+    float4* Qn = e->U(10 - e->parity);
+    // The first two steps run directly (one-time set-up calls happen there);
+    // later steps replay the captured sequence of their parity.
+    if (!e->graphs || e->steps < 2) {
+        RGF_TRY(engine_issue(e, e->graphs, n_nf, n_first, n_last, n_refill, Q, Qn));
+    } else {
+        cudaGraphExec_t& gx = e->gx[e->parity];
+        if (!gx) {
+            RGF_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            rgf_status s = engine_issue(e, true, n_nf, n_first, n_last, n_refill, Q, Qn);
+            cudaGraph_t g = nullptr;
+            cudaError_t ce = cudaStreamEndCapture(st, &g);
+            if (s != RGF_OK || ce != cudaSuccess) {
+                if (g) cudaGraphDestroy(g);
+                cudaGetLastError();
+                if (s == RGF_OK) set_error("step capture failed: %s", cudaGetErrorString(ce));
+                return s != RGF_OK ? s : RGF_E_CUDA;
+            }
+            ce = cudaGraphInstantiate(&gx, g, 0);
+            cudaGraphDestroy(g);
+            if (ce != cudaSuccess) {
+                gx = nullptr;
+                cudaGetLastError();
+                set_error("step graph instantiation failed: %s", cudaGetErrorString(ce));
+                return RGF_E_CUDA;
+            }
+        }
+        RGF_CUDA_TRY(cudaGraphLaunch(gx, st));
     }
-    if (n_first) RGF_TRY(set_identity_masked_dfc(W, bc, e->Q, d_first, st));
-    RGF_TRY(inv_mixed(c, W, W, M, gi, Rs, d_act, e->slot_flags));
-    if (n_last) {
-        RGF_TRY(sliceA(c, W, 0, e->Q, d_last));
-        RGF_TRY(sliceB(c, W, 0, gi, d_last));
-        RGF_TRY(mm(c, W, 0, 0, 1.0f, nullptr, 0, G, d_last));  // G_{0,N-1} = Q g
-        RGF_TRY(sliceA(c, W, 0, gamL, d_last));
-        RGF_TRY(sliceB(c, W, 0, G, d_last));
-        RGF_TRY(mm(c, W, 0, 0, 1.0f, nullptr, 0, Xt, d_last));
-        RGF_TRY(sliceA(c, W, 0, G, d_last));
-        RGF_TRY(sliceB(c, W, 0, gamR, d_last));
-        RGF_TRY(mm(c, W, 0, 0, 1.0f, nullptr, 0, Yt, d_last));
-        RGF_TRY(trace_masked_dfc(W, bc, Xt, Yt, d_last, e->slot_T, st));
-        RGF_TRY(engine_finish(W, e->d_tab, d_last, e->slot_T, e->slot_err, e->slot_flags, st));
-    }
+    e->parity ^= 1;
+    long long acc = 0;
+    RGF_CUDA_TRY(cudaMemcpyAsync(&acc, e->ms.reseed_acc, sizeof(acc), cudaMemcpyDeviceToHost, st));
     RGF_TRY(check_status(e));
     ++e->steps;
-    e->reseeds_seen = e->reseeds;
+    e->reseeds_seen = e->reseeds + acc;
     return RGF_OK;
 }
 
@@ -388,6 +444,7 @@ void engine_loop(Engine* e) {
                 sl.layer = 0;
                 refill[s] = 1;
                 e->h_tab[s].ready = idx;
+                e->h_tab[s].ready_D = e->ready_D;
             }
             if (sl.r)
                 ++n_active;
@@ -497,11 +554,21 @@ Engine* engine_for(Server* sv, int bc, rgf_status* st) {
         auto it = sv->engines.find(bc);
         if (it != sv->engines.end()) return it->second.get();
     }
+    ClassCfg cfg;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        auto it = sv->class_cfg.find(bc);
+        if (it != sv->class_cfg.end()) cfg = it->second;
+    }
     auto e = std::make_unique<Engine>();
     e->sv = sv;
     e->bc = bc;
-    e->W = sv->opt.slots;
+    e->W = cfg.slots > 0 ? cfg.slots : sv->opt.slots;
     *st = engine_init(e.get());
+    if (*st == RGF_OK) {
+        e->ms.bn = cfg.tile_n > 0 ? cfg.tile_n : 96;
+        e->ms.gj_nb = cfg.panel;
+    }
     if (*st != RGF_OK) {
         engine_free(e.get());
         return nullptr;
@@ -633,6 +700,22 @@ rgf_status rgf_server_create(rgf_server_t* out, const rgf_server_options* opt) {
     }
     sv->admit_th = std::thread(rgf::admit_loop, sv);
     *out = h;
+    return RGF_OK;
+}
+
+rgf_status rgf_server_set_class(rgf_server_t h, int block_class, int slots, int tile_n, int panel) {
+    if (!h || block_class < 1 || block_class > 512 || slots < 0 || slots > 4096 ||
+        (tile_n != 0 && tile_n != 64 && tile_n != 80 && tile_n != 96) || (panel != 0 && panel != 16 && panel != 32)) {
+        rgf::set_error("rgf_server_set_class: invalid arguments");
+        return RGF_E_INVALID;
+    }
+    Server* sv = &h->s;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (sv->engines.count(block_class)) {
+        rgf::set_error("rgf_server_set_class: class %d already has an engine", block_class);
+        return RGF_E_STATE;
+    }
+    sv->class_cfg[block_class] = rgf::ClassCfg{slots, tile_n, panel};
     return RGF_OK;
 }
 

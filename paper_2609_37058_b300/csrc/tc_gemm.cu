@@ -1,14 +1,15 @@
 // Slice-product complex GEMM on the Blackwell tensor cores (sm_103a).
 //
-// One CTA computes a 128 x 96 tile of the real output (128 rows, 48
-// complex columns as interleaved re/im pairs) of one batch entry:
+// One CTA computes a 128 x BN tile of the real output (128 rows, BN/2
+// complex columns as interleaved re/im pairs; BN = 64, 80 or 96 for the
+// double-float variant, 80 for the FP64 variant) of one batch entry:
 //   * TMA (cp.async.bulk.tensor, 64-byte swizzle) brings, per 32-element K
 //     chunk, the six BF16 slices of the A rows and of the B columns into
-//     shared memory; two stages, 84 KB each;
+//     shared memory; two stages (84 KB each at BN = 96);
 //   * one thread issues tcgen05.mma (kind::f16, BF16 x BF16 -> FP32,
-//     M = 128, N = 96, K = 16) for the 21 slice pairs (i, j), i + j <= 5,
+//     M = 128, N = BN, K = 16) for the 21 slice pairs (i, j), i + j <= 5,
 //     accumulating pair (i, j) in TMEM accumulator min(i + j, 4) (five
-//     accumulators x 96 columns of the 512 allocated);
+//     accumulators x BN columns of the 512 allocated);
 //   * four warps read the accumulators back with tcgen05.ld and combine
 //     the groups into double-float results (TwoSum), apply the epilogue
 //     (sign, addend, identity) and store float4 (re_hi, re_lo, im_hi, im_lo).
@@ -404,7 +405,15 @@ rgf_status oz_gemm_tc(const OzGemm& g, cudaStream_t st) {
         a.wait_ns = g.test_wait_ns;
         a.skip_first_chunk = 1;
     }
-    return launch_tc<kSlices, kGroups, 96, false>(a, st);
+    switch (g.bn) {
+        case 64: return launch_tc<kSlices, kGroups, 64, false>(a, st);
+        case 80: return launch_tc<kSlices, kGroups, 80, false>(a, st);
+        case 0:
+        case 96: return launch_tc<kSlices, kGroups, 96, false>(a, st);
+        default:
+            set_error("oz_gemm_tc: unsupported tile width %d", g.bn);
+            return RGF_E_INVALID;
+    }
 }
 
 rgf_status oz_gemm_hp(const OzGemmHP& g, cudaStream_t st) {

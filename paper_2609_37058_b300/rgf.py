@@ -108,6 +108,7 @@ def lib():
                                            ctypes.c_int]),
         "rgf_server_stats_get": (ctypes.c_int, [_P, ctypes.POINTER(rgf_server_stats)]),
         "rgf_server_destroy": (ctypes.c_int, [_P]),
+        "rgf_server_set_class": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -338,6 +339,11 @@ def rgf_server_create(opt: rgf_server_options | None = None):
     return h
 
 
+def rgf_server_set_class(server, block_class: int, slots: int = 0, tile_n: int = 0, panel: int = 0):
+    _check(lib().rgf_server_set_class(server, int(block_class), int(slots), int(tile_n), int(panel)),
+           "rgf_server_set_class")
+
+
 def rgf_server_submit(server, req: rgf_request) -> int:
     t = ctypes.c_uint64()
     _check(lib().rgf_server_submit(server, ctypes.byref(req), ctypes.byref(t)), "rgf_server_submit")
@@ -368,18 +374,38 @@ def rgf_server_destroy(server):
         _check(lib().rgf_server_destroy(server), "rgf_server_destroy")
 
 
+TUNING_PATH = os.path.join(HERE, "tuning_b300.json")
+
+
+def load_tuning(path: str = TUNING_PATH) -> dict:
+    """Per-class settings written by ``autotune`` ({} when the file is absent)."""
+    import json
+    if not os.path.exists(path):
+        return {}
+    with open(path) as f:
+        return {int(k): v for k, v in json.load(f)["classes"].items()}
+
+
 class Server:
     """Owns one rgf_server_t.  ``submit(dev, E, eta)`` takes a device
     description (as ``Plan.set_device``) and keeps its arrays alive until the
     ticket is polled; ``poll`` returns (T, err, flags, latency_ms)."""
 
     def __init__(self, slots=148, class_step=32, capacity_bytes=0, ns_steps=6, dec_tol=1e-14,
-                 dec_max_iter=100):
+                 dec_max_iter=100, tuning=None):
+        """``tuning``: {block_class: {"slots", "tile_n", "panel"}} (as written
+        by ``autotune``), "default" for the table shipped with the package,
+        or None."""
         o = rgf_server_options_default()
         o.slots, o.class_step, o.capacity_bytes = slots, class_step, capacity_bytes
         o.ns_steps, o.dec_tol, o.dec_max_iter = ns_steps, dec_tol, dec_max_iter
         self.handle = rgf_server_create(o)
         self._keep = {}
+        if tuning == "default":
+            tuning = load_tuning()
+        for bc, cfg in (tuning or {}).items():
+            rgf_server_set_class(self.handle, int(bc), cfg.get("slots", 0), cfg.get("tile_n", 0),
+                                 cfg.get("panel", 0))
 
     def submit(self, dev, E, eta) -> int:
         """Queue one device.  Host devices (numpy arrays) are read from host

@@ -117,3 +117,41 @@ def test_concurrent_engines_with_large_blocks(rgf):
     assert stats["engines"] == 4
     for (dev, E, eta), (T, err, flags, lat) in zip(jobs, res):
         assert np.abs(T - o.transmission(dev, E, eta)).max() <= MIXED_ABS, dev.b
+
+
+def test_graph_replay_matches_direct_launches(rgf, monkeypatch):
+    # Steps from the third on replay a captured CUDA graph; the same items
+    # launched directly (no graphs, host-side reseed decision) agree.
+    jobs = uneven_batch(3, 31, N_lo=6, N_hi=15, b_choices=[12, 24], n_E=9, eta=1e-6)
+    with_graphs, st = serve(rgf, jobs, slots=8, class_step=8)
+    monkeypatch.setenv("RGF_NO_GRAPHS", "1")
+    direct, _ = serve(rgf, jobs, slots=8, class_step=8)
+    assert st["steps"] > 2
+    for (dev, E, eta), a, b in zip(jobs, with_graphs, direct):
+        assert np.abs(a[0] - b[0]).max() <= 1e-12
+        assert np.abs(a[0] - o.transmission(dev, E, eta)).max() <= MIXED_ABS
+
+
+def test_class_settings_give_the_same_result(rgf):
+    # Tile width and panel width change how the work is cut, not what each
+    # product or inverse computes beyond rounding.
+    dev = random_device(8, 64, 9, metal_frac=0.25, gap_offset=0.6)
+    E = energy_grid(-1.5, 1.5, 10)
+    T_o = o.transmission(dev, E, 1e-6)
+    base = None
+    for tile_n in (64, 80, 96):
+        for panel in (16, 32):
+            (r,), _ = serve(rgf, [(dev, E, 1e-6)], slots=8, class_step=32,
+                            tuning={64: {"slots": 8, "tile_n": tile_n, "panel": panel}})
+            assert np.abs(r[0] - T_o).max() <= MIXED_ABS, (tile_n, panel)
+            if base is None:
+                base = r[0]
+            assert np.abs(r[0] - base).max() <= 1e-10, (tile_n, panel)
+    with rgf.Server(slots=8) as sv:
+        with pytest.raises(rgf.RGFError) as ex:
+            rgf.rgf_server_set_class(sv.handle, 64, 8, 72, 0)
+        assert ex.value.status == rgf.RGF_E_INVALID
+        sv.poll(sv.submit(dev, E[:2], 1e-6), timeout_us=300_000_000)
+        with pytest.raises(rgf.RGFError) as ex:
+            rgf.rgf_server_set_class(sv.handle, 64, 8, 64, 0)
+        assert ex.value.status == rgf.RGF_E_STATE
