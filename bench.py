@@ -26,9 +26,12 @@ sys.path.insert(0, ROOT)
 WORKLOAD = "doped_N500_b256"
 METRIC = "RGF energy-points/s (b=256, 500 layers), mixed vs FP64 at |dT|<=1e-6; p99 ms"
 # ncu DRAM traffic of one slice-product GEMM launch (dram__bytes_read.sum +
-# dram__bytes_write.sum) and the source it was measured on; reported only
-# while that source is unchanged.
-GEMM_TRAFFIC = None  # (bytes_per_launch, batch, sha256 of tc_gemm.cu)
+# dram__bytes_write.sum), the BF16 flops of that launch, and the source it
+# was measured on; reported (scaled by the flops of the timed launches) only
+# while that source is unchanged.  Capture: batch 148, b = 256, tile 96
+# (profiles/k_oz_tc_b256_batch148.md).
+GEMM_TRAFFIC = (699.481344e6 + 137.751296e6, 21 * 2.0 * 256 * 512 * 512 * 148,
+                "1ba293e7ff8aacb5d40fadab17ce36ca5d1e4cc8181c7ed52e9a158d81bd8a66")
 
 
 def parse():
@@ -393,6 +396,7 @@ def main():
         traffic = None
         if GEMM_TRAFFIC is not None and GEMM_TRAFFIC[2] == tc_source_hash():
             traffic = GEMM_TRAFFIC[0] * (gemm_flops / gemm_n) / GEMM_TRAFFIC[1] if gemm_n else None
+            # per launch, scaled from the captured launch by the flops ratio
         roof = {"bound": "tensor", "kernel": "k_oz_tc (slice-product GEMM, tcgen05)", "achieved": achieved,
                 "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                 "peak_source": f"bf16_tflops_sustained of {peak_src}", "launches": gemm_n,

@@ -11,7 +11,8 @@ under candidate settings and keeps the fastest, by coordinate search:
 2. the Gauss-Jordan panel width of the FP32 seed inverse (16 or 32);
 3. the number of energy slots (148, 74, then doubling from 296 while the
    rate improves, up to 1184; a candidate that does not fit in memory
-   counts as the slowest).
+   counts as the slowest); the smallest count within 3% of the best rate
+   is kept, since slots cost device memory.
 
 The figure of merit is energy points per second of wall time from
 submission to result; each candidate runs on a fresh server after a short
@@ -32,9 +33,11 @@ SLOTS = (148, 74, 296)
 MAX_SLOTS = 1184
 
 
-def search(measure, bc: int):
+def search(measure, bc: int, tol: float = 0.03):
     """Coordinate search over (tile_n, panel, slots); ``measure(bc, cfg)``
-    returns energy points per second.  Returns (best cfg, best rate, log)."""
+    returns energy points per second.  The slot count kept is the smallest
+    whose rate is within ``tol`` of the best one measured (slots cost device
+    memory).  Returns (best cfg, its rate, log)."""
     log = []
 
     def run(cfg):
@@ -44,24 +47,33 @@ def search(measure, bc: int):
 
     cfg = {"tile_n": TILES[0], "panel": PANELS[0], "slots": SLOTS[0]}
     best = run(cfg)
+    slot_rates = {cfg["slots"]: best}
     for key, values in (("tile_n", TILES), ("panel", PANELS), ("slots", SLOTS)):
         for v in values:
             if v == cfg[key]:
                 continue
             trial = dict(cfg, **{key: v})
             rate = run(trial)
+            if key == "slots":
+                slot_rates[v] = rate
             if rate > best:
                 best, cfg = rate, trial
+        if key == "panel":
+            slot_rates = {cfg["slots"]: best}
     # More slots keep paying while the launches are not yet full.
-    while cfg["slots"] == max(SLOTS) or (cfg["slots"] > max(SLOTS) and cfg["slots"] < MAX_SLOTS):
-        trial = dict(cfg, slots=cfg["slots"] * 2)
-        if trial["slots"] > MAX_SLOTS:
-            break
+    s = max(SLOTS)
+    while cfg["slots"] == s and s * 2 <= MAX_SLOTS:
+        s *= 2
+        trial = dict(cfg, slots=s)
         rate = run(trial)
+        slot_rates[s] = rate
         if rate <= best:
             break
         best, cfg = rate, trial
-    return cfg, best, log
+    keep = min(n for n, r in slot_rates.items() if r >= (1.0 - tol) * best)
+    if keep != cfg["slots"]:
+        cfg = dict(cfg, slots=keep)
+    return cfg, slot_rates[keep], log
 
 
 def gpu_measure(layers: int, energies: int, eta: float = 1e-5):

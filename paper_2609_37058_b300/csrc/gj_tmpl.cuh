@@ -4,6 +4,7 @@
 #pragma once
 
 #include <atomic>
+#include <type_traits>
 
 #include "kernels.h"
 
@@ -104,6 +105,84 @@ rgf_status zgemm_t(const GemmArgs<T2>& g, cudaStream_t st) {
     return RGF_OK;
 }
 
+// Trailing update of the FP32 Gauss-Jordan inverse: C += A B for one batch
+// entry per blockIdx.z, with A m x K (K <= 32, row-major, lda = K), B K x n
+// (row-major, ldb = ldc) and columns [skip0, skip1) of C left alone.  K is
+// small, so the whole A and B tiles are staged in shared memory at once; a
+// CTA owns 128 x 64 complex outputs, a thread 8 x 4 of them.
+constexpr int GU_BM = 128, GU_BN = 64, GU_KMAX = 32, GU_AP = GU_KMAX + 1;
+constexpr size_t GU_SMEM = (size_t)(GU_BM * GU_AP + GU_KMAX * GU_BN) * sizeof(float2);
+
+static __global__ void __launch_bounds__(256) k_gj_update_f32(int m, int n, int K, const float2* __restrict__ A, long sA,
+                                                       const float2* __restrict__ B, long sB, float2* C, long ldc,
+                                                       long sC, int skip0, int skip1, const int* active) {
+    const int bi = blockIdx.z;
+    if (active && !active[bi]) return;
+    const int m0 = blockIdx.y * GU_BM, n0 = blockIdx.x * GU_BN;
+    if (n0 >= skip0 && n0 + GU_BN <= skip1) return;
+    extern __shared__ __align__(16) unsigned char gu_smem[];
+    float2* As = reinterpret_cast<float2*>(gu_smem);  // [GU_BM][GU_AP]
+    float2* Bs = As + GU_BM * GU_AP;                   // [GU_KMAX][GU_BN]
+    const float2* Ab = A + (long)bi * sA;
+    const float2* Bb = B + (long)bi * sB;
+    const int tid = threadIdx.x;
+    for (int i = tid; i < GU_BM * K; i += 256) {
+        const int r = i / K, k = i - r * K;
+        As[r * GU_AP + k] = (m0 + r < m) ? Ab[(long)(m0 + r) * K + k] : make_float2(0.f, 0.f);
+    }
+    for (int i = tid; i < K * GU_BN; i += 256) {
+        const int k = i / GU_BN, c = i - k * GU_BN;
+        Bs[k * GU_BN + c] = (n0 + c < n) ? Bb[(long)k * ldc + n0 + c] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    const int tx = tid & 15, ty = tid >> 4;
+    float2 acc[8][4];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
+    for (int k = 0; k < K; ++k) {
+        float2 a[8], b[4];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) a[i] = As[(ty + 16 * i) * GU_AP + k];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) b[j] = Bs[k * GU_BN + tx + 16 * j];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) cfma(acc[i][j], a[i], b[j]);
+    }
+    float2* Cb = C + (long)bi * sC;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int r = m0 + ty + 16 * i;
+        if (r >= m) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int c = n0 + tx + 16 * j;
+            if (c >= n || (c >= skip0 && c < skip1)) continue;
+            float2 v = Cb[(long)r * ldc + c];
+            v.x += acc[i][j].x;
+            v.y += acc[i][j].y;
+            Cb[(long)r * ldc + c] = v;
+        }
+    }
+}
+
+static rgf_status gj_update_f32(int batch, int m, int n, int K, const float2* A, long sA, const float2* B, long sB,
+                                float2* C, long ldc, long sC, int skip0, int skip1, const int* active,
+                                cudaStream_t st) {
+    static std::atomic<bool> attr{false};
+    if (!attr.load()) {
+        RGF_CUDA_TRY(cudaFuncSetAttribute(k_gj_update_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GU_SMEM));
+        attr.store(true);
+    }
+    dim3 grid(ceil_div(n, GU_BN), ceil_div(m, GU_BM), batch);
+    k_gj_update_f32<<<grid, 256, GU_SMEM, st>>>(m, n, K, A, sA, B, sB, C, ldc, sC, skip0, skip1, active);
+    RGF_LAUNCH_CHECK();
+    return RGF_OK;
+}
+
 // ------------------------------------------------------------------ inverse
 // Blocked Gauss-Jordan with partial pivoting, in place.  For each panel of
 // nb columns K = [k0, k0+nb):
@@ -132,90 +211,125 @@ __device__ __forceinline__ void argmax_merge(R& v, int& i, R v2, int i2) {
     }
 }
 
-// Panel kernel: 256 threads; lane = panel column (NB <= 32), warp w owns rows
-// w, w + 8, ...  The panel lives in shared memory with a row pitch of NB + 1
-// elements so that column reads are (almost) free of bank conflicts.
+template <typename T2>
+__device__ __forceinline__ T2 shfl_c(T2 v, int src) {
+    v.x = __shfl_sync(0xffffffffu, v.x, src);
+    v.y = __shfl_sync(0xffffffffu, v.y, src);
+    return v;
+}
+
+// Panel kernel: 256 threads; lane = panel column (NB <= 32), warp w owns
+// rows w, w + 8, ...  The panel lives in shared memory with a row pitch of
+// NB + 1 elements; the pivot column is copied to a separate array (fcol) so
+// that the rank-1 update reads and writes never alias and can be pipelined.
+// One pivot step costs two block barriers: the pivot search of the next
+// column is folded into the update (the lane that owns that column tracks
+// its warp's largest candidate), and warp 0 swaps and scales the pivot row
+// while the other warps copy their part of the pivot column.
+constexpr int GJ_WARPS = 8;
 template <typename T2, int NB>
 __global__ void __launch_bounds__(256) k_gj_panel(int b, int k0, int nbk, T2* A, long sA, T2* Pbar, int* piv,
                                                   int* flags, const int* active) {
     using C = CT<T2>;
     using R = typename C::R;
-    constexpr int P = NB + 1;
+    constexpr int P = NB + 1, NW = GJ_WARPS;
     const int bi = blockIdx.x;
     if (active && !active[bi]) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T2* pan = reinterpret_cast<T2*>(smem_raw);  // b x P
     T2* fcol = pan + (long)b * P;                // b
-    __shared__ R red_v[8];
-    __shared__ int red_i[8];
-    __shared__ int s_piv;
+    __shared__ R red_v[2][NW];
+    __shared__ int red_i[2][NW];
     T2* Ab = A + (long)bi * sA;
     int* pv = piv + (long)bi * b;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const bool col_ok = lane < nbk;
+    const T2 zero = C::make(0, 0);
 
-    for (int r = wid; r < b; r += 8)
+    for (int r = wid; r < b; r += NW)
         if (col_ok) pan[r * P + lane] = Ab[(long)r * b + k0 + lane];
+    __syncthreads();
+    {
+        // Candidates of the first column: rows k0 .. b-1.
+        R bv = -1;
+        int bix = b;
+        for (int r = k0 + tid; r < b; r += 32 * NW) argmax_merge<R>(bv, bix, cabs2(pan[r * P]), r);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const R ov = __shfl_down_sync(0xffffffffu, bv, off);
+            const int oi = __shfl_down_sync(0xffffffffu, bix, off);
+            argmax_merge<R>(bv, bix, ov, oi);
+        }
+        if (lane == 0) {
+            red_v[0][wid] = bv;
+            red_i[0][wid] = bix;
+        }
+    }
     __syncthreads();
 
     for (int jj = 0; jj < nbk; ++jj) {
-        const int j = k0 + jj;
-        R bv = -1;
-        int bidx = b;
-        for (int r = j + tid; r < b; r += 256) argmax_merge<R>(bv, bidx, cabs2(pan[r * P + jj]), r);
+        const int j = k0 + jj, buf = jj & 1;
+        R v = red_v[buf][0];
+        int p = red_i[buf][0];
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            R ov = __shfl_down_sync(0xffffffffu, bv, off);
-            int oi = __shfl_down_sync(0xffffffffu, bidx, off);
-            argmax_merge<R>(bv, bidx, ov, oi);
-        }
-        if (lane == 0) {
-            red_v[wid] = bv;
-            red_i[wid] = bidx;
-        }
-        __syncthreads();
+        for (int w = 1; w < NW; ++w) argmax_merge<R>(v, p, red_v[buf][w], red_i[buf][w]);
+        if (p >= b) p = j;
         if (tid == 0) {
-            R v = red_v[0];
-            int ix = red_i[0];
-            for (int w = 1; w < 8; ++w) argmax_merge<R>(v, ix, red_v[w], red_i[w]);
-            if (ix >= b) ix = j;
-            s_piv = ix;
-            pv[j] = ix;
+            pv[j] = p;
             if (!(v > 0) && flags) atomicOr(&flags[bi], RGF_FLAG_SINGULAR);
         }
-        __syncthreads();
-        const int p = s_piv;
-        if (p != j && tid < nbk) {
-            T2 t = pan[j * P + tid];
-            pan[j * P + tid] = pan[p * P + tid];
-            pan[p * P + tid] = t;
+        // Pivot column of the rows other than j and p (unchanged by the swap).
+        for (int r = wid + 32 * 0 + lane * NW; r < b; r += 32 * NW)
+            if (r != j && r != p) fcol[r] = pan[r * P + jj];
+        if (wid == 0) {
+            // Row p becomes the pivot row j, scaled by the inverse pivot;
+            // the old row j moves to position p.
+            const T2 rj = col_ok ? pan[j * P + lane] : zero;
+            const T2 rp = col_ok ? pan[p * P + lane] : zero;
+            const T2 inv_d = cinv(shfl_c(rp, jj));
+            const T2 rj_jj = shfl_c(rj, jj);
+            if (col_ok) {
+                pan[j * P + lane] = (lane == jj) ? inv_d : cmul(rp, inv_d);
+                if (p != j) pan[p * P + lane] = rj;
+            }
+            if (lane == 0 && p != j) fcol[p] = rj_jj;
         }
         __syncthreads();
-        const T2 inv_d = cinv(pan[j * P + jj]);
-        for (int r = tid; r < b; r += 256) fcol[r] = pan[r * P + jj];
-        __syncthreads();
-        if (tid < nbk) pan[j * P + tid] = (tid == jj) ? inv_d : cmul(pan[j * P + tid], inv_d);
-        __syncthreads();
+        const T2 pj = col_ok ? pan[j * P + lane] : zero;
+        const T2 inv_d = pan[j * P + jj];
+        const bool next = jj + 1 < nbk;
+        const bool track = next && lane == jj + 1;
+        R bv = -1;
+        int bix = b;
         if (col_ok) {
-            const T2 pj = pan[j * P + lane];
-            for (int r = wid; r < b; r += 8) {
+#pragma unroll 4
+            for (int r = wid; r < b; r += NW) {
                 if (r == j) continue;
                 const T2 f = fcol[r];
                 if (lane == jj) {
                     pan[r * P + lane] = cmul(C::make(-f.x, -f.y), inv_d);
                 } else {
-                    T2 v = pan[r * P + lane];
-                    v.x -= f.x * pj.x - f.y * pj.y;
-                    v.y -= f.x * pj.y + f.y * pj.x;
-                    pan[r * P + lane] = v;
+                    T2 y = pan[r * P + lane];
+                    y.x -= f.x * pj.x - f.y * pj.y;
+                    y.y -= f.x * pj.y + f.y * pj.x;
+                    pan[r * P + lane] = y;
+                    if (track && r > j) argmax_merge<R>(bv, bix, cabs2(y), r);
                 }
+            }
+        }
+        if (next) {
+            const R v2 = __shfl_sync(0xffffffffu, bv, jj + 1);
+            const int i2 = __shfl_sync(0xffffffffu, bix, jj + 1);
+            if (lane == 0) {
+                red_v[buf ^ 1][wid] = v2;
+                red_i[buf ^ 1][wid] = i2;
             }
         }
         __syncthreads();
     }
     T2* Pb = Pbar + (long)bi * b * nbk;
     if (col_ok) {
-        for (int r = wid; r < b; r += 8) {
+        for (int r = wid; r < b; r += NW) {
             T2 v = pan[r * P + lane];
             Ab[(long)r * b + k0 + lane] = v;
             if (r == k0 + lane) v.x -= 1;
@@ -325,6 +439,11 @@ rgf_status inv_t(int batch, int b, T2* A, long sA, void* ws, int* flags, const i
             dim3 g2(ceil_div(b, 128), batch);
             k_gj_swap<T2><<<g2, 128, 0, st>>>(b, k0, nbk, A, sA, piv, T, active);
             RGF_LAUNCH_CHECK();
+            if constexpr (std::is_same<T2, float2>::value) {
+                RGF_TRY(gj_update_f32(batch, b, b, nbk, Pbar, (long)b * nbk, T, (long)nbk * b, A, b, sA, k0,
+                                      k0 + nbk, active, st));
+                continue;
+            }
             GemmArgs<T2> g{};
             g.batch = batch;
             g.m = b;

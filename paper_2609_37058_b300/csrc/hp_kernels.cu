@@ -90,55 +90,63 @@ __global__ void __launch_bounds__(256) k_slice_rows_f64(int m, int k, const doub
     }
 }
 
-__global__ void k_colexp_f64(int k, int n, const double2* __restrict__ B, long sB, int* __restrict__ colexp,
-                             const int* __restrict__ active) {
-    const int bi = blockIdx.y;
-    if (active && !active[bi]) return;
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= n) return;
-    const double2* Bb = B + (long)bi * sB;
-    double mx = 0.0;
-    for (int j = 0; j < k; ++j) {
-        const double2 v = Bb[(long)j * n + c];
-        mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
-    }
-    colexp[(long)bi * n + c] = exp_above_f64(mx);
-}
-
+// One CTA per strip of 32 columns: column exponents first, then 32 x 32
+// tiles through shared memory (layout as the double-float column slicer).
 __global__ void __launch_bounds__(256) k_slice_cols_f64(int k, int n, const double2* __restrict__ B, long sB,
                                                         __nv_bfloat16* __restrict__ out, int Kp,
-                                                        const int* __restrict__ colexp,
                                                         const int* __restrict__ active) {
-    const int bi = blockIdx.z;
+    const int bi = blockIdx.y;
     if (active && !active[bi]) return;
     __shared__ double2 tile[32][33];
-    const int j0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+    __shared__ double cmax[8][32];
+    __shared__ int cexp[32];
+    const int c0 = blockIdx.x * 32;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
     const double2* Bb = B + (long)bi * sB;
-    for (int jj = ty; jj < 32; jj += 8) {
-        const int j = j0 + jj, c = c0 + tx;
-        tile[jj][tx] = (j < k && c < n) ? Bb[(long)j * n + c] : make_double2(0.0, 0.0);
+    {
+        const int c = c0 + tx;
+        double mx = 0.0;
+        if (c < n)
+            for (int j = ty; j < k; j += 8) {
+                const double2 v = Bb[(long)j * n + c];
+                mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+            }
+        cmax[ty][tx] = mx;
     }
     __syncthreads();
-    const long rows = 2L * n;
-    for (int cc = ty; cc < 32; cc += 8) {
-        const int c = c0 + cc, j = j0 + tx;
-        if (c >= n || j >= k) continue;
-        const double2 v = tile[tx][cc];
-        const int e = colexp[(long)bi * n + c];
-        float sr[kSlicesHP], si[kSlicesHP];
-        digits7(v.x, e, sr);
-        digits7(v.y, e, si);
+    if (ty == 0) {
+        double mx = cmax[0][tx];
 #pragma unroll
-        for (int s = 0; s < kSlicesHP; ++s) {
-            __nv_bfloat16* base = out + (((long)bi * kSlicesHP + s) * rows) * Kp;
-            __nv_bfloat162 p0, p1;
-            p0.x = __float2bfloat16_rn(sr[s]);
-            p0.y = __float2bfloat16_rn(-si[s]);
-            p1.x = __float2bfloat16_rn(si[s]);
-            p1.y = __float2bfloat16_rn(sr[s]);
-            *reinterpret_cast<__nv_bfloat162*>(base + (2L * c) * Kp + 2 * j) = p0;
-            *reinterpret_cast<__nv_bfloat162*>(base + (2L * c + 1) * Kp + 2 * j) = p1;
+        for (int w = 1; w < 8; ++w) mx = fmax(mx, cmax[w][tx]);
+        cexp[tx] = exp_above_f64(mx);
+    }
+    const long rows = 2L * n;
+    for (int j0 = 0; j0 < k; j0 += 32) {
+        __syncthreads();
+        for (int jj = ty; jj < 32; jj += 8) {
+            const int j = j0 + jj, c = c0 + tx;
+            tile[jj][tx] = (j < k && c < n) ? Bb[(long)j * n + c] : make_double2(0.0, 0.0);
+        }
+        __syncthreads();
+        for (int cc = ty; cc < 32; cc += 8) {
+            const int c = c0 + cc, j = j0 + tx;
+            if (c >= n || j >= k) continue;
+            const double2 v = tile[tx][cc];
+            const int e = cexp[cc];
+            float sr[kSlicesHP], si[kSlicesHP];
+            digits7(v.x, e, sr);
+            digits7(v.y, e, si);
+#pragma unroll
+            for (int s = 0; s < kSlicesHP; ++s) {
+                __nv_bfloat16* base = out + (((long)bi * kSlicesHP + s) * rows) * Kp;
+                __nv_bfloat162 p0, p1;
+                p0.x = __float2bfloat16_rn(sr[s]);
+                p0.y = __float2bfloat16_rn(-si[s]);
+                p1.x = __float2bfloat16_rn(si[s]);
+                p1.y = __float2bfloat16_rn(sr[s]);
+                *reinterpret_cast<__nv_bfloat162*>(base + (2L * c) * Kp + 2 * j) = p0;
+                *reinterpret_cast<__nv_bfloat162*>(base + (2L * c + 1) * Kp + 2 * j) = p1;
+            }
         }
     }
 }
@@ -156,10 +164,8 @@ rgf_status slice_rows_f64(int batch, int m, int k, const double2* A, long sA, __
 rgf_status slice_cols_f64(int batch, int k, int n, const double2* B, long sB, __nv_bfloat16* out, int Kp,
                           int* colexp, const int* active, cudaStream_t st) {
     if (batch <= 0) return RGF_OK;
-    k_colexp_f64<<<dim3(ceil_div(n, 128), batch), 128, 0, st>>>(k, n, B, sB, colexp, active);
-    RGF_LAUNCH_CHECK();
-    k_slice_cols_f64<<<dim3(ceil_div(k, 32), ceil_div(n, 32), batch), 256, 0, st>>>(k, n, B, sB, out, Kp, colexp,
-                                                                                   active);
+    (void)colexp;
+    k_slice_cols_f64<<<dim3(ceil_div(n, 32), batch), 256, 0, st>>>(k, n, B, sB, out, Kp, active);
     RGF_LAUNCH_CHECK();
     return RGF_OK;
 }

@@ -88,57 +88,65 @@ rgf_status slice_rows(int batch, int m, int k, const float4* A, long sA, __nv_bf
     return RGF_OK;
 }
 
-__global__ void k_colexp(int k, int n, const float4* __restrict__ B, long sB, int* __restrict__ colexp,
-                         const int* __restrict__ active) {
-    const int bi = blockIdx.y;
-    if (active && !active[bi]) return;
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= n) return;
-    const float4* Bb = B + (long)bi * sB;
-    float mx = 0.0f;
-    for (int j = 0; j < k; ++j) {
-        const float4 v = Bb[(long)j * n + c];
-        mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.z)));
-    }
-    colexp[(long)bi * n + c] = exp_above(mx);
-}
-
-// 32 (j) x 32 (c) tiles through shared memory so that both the df reads
-// (along c) and the slice writes (along j) are coalesced.
+// One CTA per strip of 32 columns of one batch entry: first the column
+// maxima (exponents) over all k rows, then 32 (j) x 32 (c) tiles through
+// shared memory so that both the df reads (along c) and the slice writes
+// (along j) are coalesced.  The second pass re-reads the strip from L2.
 __global__ void __launch_bounds__(256) k_slice_cols(int k, int n, const float4* __restrict__ B, long sB,
                                                     __nv_bfloat16* __restrict__ out, int Kp,
-                                                    const int* __restrict__ colexp,
                                                     const int* __restrict__ active) {
-    const int bi = blockIdx.z;
+    const int bi = blockIdx.y;
     if (active && !active[bi]) return;
     __shared__ float4 tile[32][33];
-    const int j0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+    __shared__ float cmax[8][32];
+    __shared__ int cexp[32];
+    const int c0 = blockIdx.x * 32;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
     const float4* Bb = B + (long)bi * sB;
-    for (int jj = ty; jj < 32; jj += 8) {
-        const int j = j0 + jj, c = c0 + tx;
-        tile[jj][tx] = (j < k && c < n) ? Bb[(long)j * n + c] : make_float4(0.f, 0.f, 0.f, 0.f);
+    {
+        const int c = c0 + tx;
+        float mx = 0.0f;
+        if (c < n)
+            for (int j = ty; j < k; j += 8) {
+                const float4 v = Bb[(long)j * n + c];
+                mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.z)));
+            }
+        cmax[ty][tx] = mx;
     }
     __syncthreads();
-    const long rows = 2L * n;
-    for (int cc = ty; cc < 32; cc += 8) {
-        const int c = c0 + cc, j = j0 + tx;
-        if (c >= n || j >= k) continue;
-        const float4 v = tile[tx][cc];
-        const int e = colexp[(long)bi * n + c];
-        float sr[kSlices], si[kSlices];
-        slice6(v.x, v.y, e, sr);
-        slice6(v.z, v.w, e, si);
+    if (ty == 0) {
+        float mx = cmax[0][tx];
 #pragma unroll
-        for (int s = 0; s < kSlices; ++s) {
-            __nv_bfloat16* base = out + (((long)bi * kSlices + s) * rows) * Kp;
-            __nv_bfloat162 p0, p1;
-            p0.x = __float2bfloat16_rn(sr[s]);
-            p0.y = __float2bfloat16_rn(-si[s]);
-            p1.x = __float2bfloat16_rn(si[s]);
-            p1.y = __float2bfloat16_rn(sr[s]);
-            *reinterpret_cast<__nv_bfloat162*>(base + (2L * c) * Kp + 2 * j) = p0;
-            *reinterpret_cast<__nv_bfloat162*>(base + (2L * c + 1) * Kp + 2 * j) = p1;
+        for (int w = 1; w < 8; ++w) mx = fmaxf(mx, cmax[w][tx]);
+        cexp[tx] = exp_above(mx);
+    }
+    const long rows = 2L * n;
+    for (int j0 = 0; j0 < k; j0 += 32) {
+        __syncthreads();
+        for (int jj = ty; jj < 32; jj += 8) {
+            const int j = j0 + jj, c = c0 + tx;
+            tile[jj][tx] = (j < k && c < n) ? Bb[(long)j * n + c] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        __syncthreads();
+        for (int cc = ty; cc < 32; cc += 8) {
+            const int c = c0 + cc, j = j0 + tx;
+            if (c >= n || j >= k) continue;
+            const float4 v = tile[tx][cc];
+            const int e = cexp[cc];
+            float sr[kSlices], si[kSlices];
+            slice6(v.x, v.y, e, sr);
+            slice6(v.z, v.w, e, si);
+#pragma unroll
+            for (int s = 0; s < kSlices; ++s) {
+                __nv_bfloat16* base = out + (((long)bi * kSlices + s) * rows) * Kp;
+                __nv_bfloat162 p0, p1;
+                p0.x = __float2bfloat16_rn(sr[s]);
+                p0.y = __float2bfloat16_rn(-si[s]);
+                p1.x = __float2bfloat16_rn(si[s]);
+                p1.y = __float2bfloat16_rn(sr[s]);
+                *reinterpret_cast<__nv_bfloat162*>(base + (2L * c) * Kp + 2 * j) = p0;
+                *reinterpret_cast<__nv_bfloat162*>(base + (2L * c + 1) * Kp + 2 * j) = p1;
+            }
         }
     }
 }
@@ -146,10 +154,8 @@ __global__ void __launch_bounds__(256) k_slice_cols(int k, int n, const float4* 
 rgf_status slice_cols(int batch, int k, int n, const float4* B, long sB, __nv_bfloat16* out, int Kp, int* colexp,
                       const int* active, cudaStream_t st) {
     if (batch <= 0) return RGF_OK;
-    k_colexp<<<dim3(ceil_div(n, 128), batch), 128, 0, st>>>(k, n, B, sB, colexp, active);
-    RGF_LAUNCH_CHECK();
-    k_slice_cols<<<dim3(ceil_div(k, 32), ceil_div(n, 32), batch), 256, 0, st>>>(k, n, B, sB, out, Kp, colexp,
-                                                                               active);
+    (void)colexp;
+    k_slice_cols<<<dim3(ceil_div(n, 32), batch), 256, 0, st>>>(k, n, B, sB, out, Kp, active);
     RGF_LAUNCH_CHECK();
     return RGF_OK;
 }

@@ -7,12 +7,15 @@
 
 namespace rgf {
 
-constexpr int kPoolUnits = 24;  // df matrices, in units of W
+constexpr int kPoolUnits = 20;  // df matrices, in units of W
 constexpr int kDecUnits = 24;   // FP64 decimation matrices, in units of W
 
-// Workspace of W energies (2W lead entries) of block size b.
+// Workspace of W energies of block size b, with lead decimation for Wd
+// energies (2 Wd lead entries) at a time.
 struct MixedState {
-    int b = 0, W = 0, Kp = 0;
+    int b = 0, W = 0, Wd = 0, Kp = 0;
+    int slice_entries = 0;   // batch entries the df slice buffers hold (W or 2W)
+    int inv_entries = 0;     // batch entries of the inverse workspaces
     float4* pool = nullptr;  // kPoolUnits * W df matrices
     __nv_bfloat16* sa[2] = {};
     __nv_bfloat16* sb[2] = {};
@@ -46,14 +49,21 @@ struct MixedState {
     void* dec_own = nullptr;
 };
 
-// Bytes of the carved workspace (without the decimation pool).
+// Bytes of the carved workspace (without the decimation pool) for W energies
+// whose df slice buffers hold slice_entries (W or 2W) batch entries and
+// whose inverse workspaces hold inv_entries.  The two-argument form is the
+// single-device plan's (slice and inverse buffers for 2W entries).
+size_t mixed_workspace_bytes(int W, int b, int slice_entries, int inv_entries);
 size_t mixed_workspace_bytes(int W, int b);
-// Bytes of the decimation pool and its slice buffers.
-size_t mixed_dec_bytes(int W, int b);
-// Set up m for W energies of block size b.  ws (mixed_workspace_bytes) may be
-// null, in which case the state allocates it.  The decimation pool and the
-// small buffers are always allocated by the state.
-rgf_status mixed_state_init(MixedState* m, int b, int W, void* ws, cudaStream_t st);
+// Bytes of the decimation pool and its slice buffers for Wd energies.
+size_t mixed_dec_bytes(int Wd, int b);
+// Set up m for W energies of block size b and decimation batches of Wd
+// energies (Wd <= W; 0 = W).  slice_entries: W when only W-entry products
+// are sliced in double-float (the server's engines), 2W for the plan.  ws
+// (mixed_workspace_bytes) may be null, in which case the state allocates it.
+// The decimation pool and the small buffers are always allocated by the state.
+rgf_status mixed_state_init(MixedState* m, int b, int W, void* ws, cudaStream_t st, int Wd = 0,
+                            int slice_entries = 0);
 void mixed_state_free(MixedState* m);
 
 // What one batch of refined inverses writes besides X.

@@ -4,6 +4,7 @@
 // X <- X + X (I - M X) whose residual and correction are again slice
 // products.  Matrices between kernels are double-float complex (float4).
 // The final Caroli trace is reduced in FP64.
+#include <algorithm>
 #include <cstdlib>
 #include <utility>
 #include <vector>
@@ -227,26 +228,35 @@ rgf_status inv_mixed(const Ctx& c, int cnt, int W, const float4* M, float4* X, f
     return RGF_OK;
 }
 
-size_t mixed_workspace_bytes(int W, int b) {
+size_t mixed_workspace_bytes(int W, int b, int slice_entries, int inv_entries) {
     const int Kp = slice_pitch(b);
     const size_t nn = (size_t)b * b;
     size_t s = (size_t)kPoolUnits * W * nn * sizeof(float4);
-    s += 2 * sa_bytes(2 * W, b, Kp) + 2 * sb_bytes(2 * W, b, Kp);
-    s += (size_t)2 * W * nn * sizeof(float2) + inv_workspace_bytes_t<float2>(2 * W, b);
-    s += (size_t)2 * W * nn * sizeof(double2) + inv_workspace_bytes_t<double2>(2 * W, b);
-    s += (size_t)2 * W * b * sizeof(int) + (size_t)2 * W * 3 * sizeof(int) + (size_t)2 * W * sizeof(double2) + 8192;
+    s += 2 * sa_bytes(slice_entries, b, Kp) + 2 * sb_bytes(slice_entries, b, Kp);
+    s += (size_t)inv_entries * nn * sizeof(float2) + inv_workspace_bytes_t<float2>(inv_entries, b);
+    s += (size_t)inv_entries * nn * sizeof(double2) + inv_workspace_bytes_t<double2>(inv_entries, b);
+    s += (size_t)inv_entries * b * sizeof(int) + (size_t)inv_entries * 3 * sizeof(int) +
+         (size_t)inv_entries * sizeof(double2) + 8192;
     return s;
 }
 
-size_t mixed_dec_bytes(int W, int b) {
+size_t mixed_workspace_bytes(int W, int b) { return mixed_workspace_bytes(W, b, 2 * W, 2 * W); }
+
+size_t mixed_dec_bytes(int Wd, int b) {
     const int Kp = slice_pitch(b);
-    return (size_t)kDecUnits * W * b * b * sizeof(double2) + 2 * sa_bytes(2 * W, b, Kp, kSlicesHP) +
-           2 * sb_bytes(2 * W, b, Kp, kSlicesHP) + (size_t)2 * W * (3 * sizeof(int) + sizeof(double)) + 4096;
+    return (size_t)kDecUnits * Wd * b * b * sizeof(double2) + 2 * sa_bytes(2 * Wd, b, Kp, kSlicesHP) +
+           2 * sb_bytes(2 * Wd, b, Kp, kSlicesHP) + (size_t)2 * Wd * (3 * sizeof(int) + sizeof(double)) + 4096;
 }
 
-rgf_status mixed_state_init(MixedState* m, int b, int W, void* ws, cudaStream_t st) {
+rgf_status mixed_state_init(MixedState* m, int b, int W, void* ws, cudaStream_t st, int Wd, int slice_entries) {
+    if (Wd <= 0 || Wd > W) Wd = W;
+    if (slice_entries <= 0) slice_entries = 2 * W;
+    const int inv_entries = std::max(W, 2 * Wd);
     m->b = b;
     m->W = W;
+    m->Wd = Wd;
+    m->slice_entries = slice_entries;
+    m->inv_entries = inv_entries;
     m->Kp = slice_pitch(b);
     const size_t nn = (size_t)b * b;
     const char* env = getenv("RGF_OZ_CORE");
@@ -260,7 +270,7 @@ rgf_status mixed_state_init(MixedState* m, int b, int W, void* ws, cudaStream_t 
         return RGF_OK;
     };
     if (!ws) {
-        RGF_TRY(alloc(&m->own, mixed_workspace_bytes(W, b)));
+        RGF_TRY(alloc(&m->own, mixed_workspace_bytes(W, b, slice_entries, inv_entries)));
         ws = m->own;
     }
     // Carve the workspace.
@@ -269,64 +279,65 @@ rgf_status mixed_state_init(MixedState* m, int b, int W, void* ws, cudaStream_t 
     w += (size_t)kPoolUnits * W * nn * sizeof(float4);
     for (int i = 0; i < 2; ++i) {
         m->sa[i] = (__nv_bfloat16*)w;
-        w += sa_bytes(2 * W, b, m->Kp);
+        w += sa_bytes(slice_entries, b, m->Kp);
     }
     for (int i = 0; i < 2; ++i) {
         m->sb[i] = (__nv_bfloat16*)w;
-        w += sb_bytes(2 * W, b, m->Kp);
+        w += sb_bytes(slice_entries, b, m->Kp);
     }
     m->c64 = (float2*)w;
-    w += (size_t)2 * W * nn * sizeof(float2);
+    w += (size_t)inv_entries * nn * sizeof(float2);
     m->inv_ws = (void*)w;
-    w += inv_workspace_bytes_t<float2>(2 * W, b);
+    w += inv_workspace_bytes_t<float2>(inv_entries, b);
     w = (char*)(((uintptr_t)w + 255) & ~(uintptr_t)255);
     m->c128 = (double2*)w;
-    w += (size_t)2 * W * nn * sizeof(double2);
+    w += (size_t)inv_entries * nn * sizeof(double2);
     m->inv64_ws = (void*)w;
-    w += inv_workspace_bytes_t<double2>(2 * W, b);
+    w += inv_workspace_bytes_t<double2>(inv_entries, b);
     w = (char*)(((uintptr_t)w + 255) & ~(uintptr_t)255);
     m->nsact[0] = (int*)w;
-    w += (size_t)2 * W * sizeof(int);
+    w += (size_t)inv_entries * sizeof(int);
     m->nsact[1] = (int*)w;
-    w += (size_t)2 * W * sizeof(int);
+    w += (size_t)inv_entries * sizeof(int);
     m->bad = (int*)w;
-    w += (size_t)2 * W * sizeof(int);
+    w += (size_t)inv_entries * sizeof(int);
     w = (char*)(((uintptr_t)w + 15) & ~(uintptr_t)15);
     m->theta = (double2*)w;
-    w += (size_t)2 * W * sizeof(double2);
+    w += (size_t)inv_entries * sizeof(double2);
     w = (char*)(((uintptr_t)w + 255) & ~(uintptr_t)255);
     m->colexp = (int*)w;
     // Zero the slice buffers once: the K padding is never written again.
-    RGF_CUDA_TRY(cudaMemsetAsync(m->sa[0], 0, 2 * sa_bytes(2 * W, b, m->Kp) + 2 * sb_bytes(2 * W, b, m->Kp), st));
+    RGF_CUDA_TRY(cudaMemsetAsync(m->sa[0], 0,
+                                 2 * sa_bytes(slice_entries, b, m->Kp) + 2 * sb_bytes(slice_entries, b, m->Kp), st));
     RGF_TRY(alloc((void**)&m->status, 4 * sizeof(int)));
     m->bad_count = m->status + 1;
     m->reseed_acc = (long long*)(m->status + 2);
     {
         char* d = nullptr;
-        RGF_TRY(alloc((void**)&d, mixed_dec_bytes(W, b)));
+        RGF_TRY(alloc((void**)&d, mixed_dec_bytes(Wd, b)));
         m->dec_own = d;
         m->dec_pool = (double2*)d;
-        d += (size_t)kDecUnits * W * nn * sizeof(double2);
+        d += (size_t)kDecUnits * Wd * nn * sizeof(double2);
         for (int i = 0; i < 2; ++i) {
             m->hsa[i] = (__nv_bfloat16*)d;
-            d += sa_bytes(2 * W, b, m->Kp, kSlicesHP);
+            d += sa_bytes(2 * Wd, b, m->Kp, kSlicesHP);
         }
         for (int i = 0; i < 2; ++i) {
             m->hsb[i] = (__nv_bfloat16*)d;
-            d += sb_bytes(2 * W, b, m->Kp, kSlicesHP);
+            d += sb_bytes(2 * Wd, b, m->Kp, kSlicesHP);
         }
         m->dec_anorm = (double*)d;
-        d += (size_t)2 * W * sizeof(double);
+        d += (size_t)2 * Wd * sizeof(double);
         m->dec_active = (int*)d;
-        d += (size_t)2 * W * sizeof(int);
+        d += (size_t)2 * Wd * sizeof(int);
         m->dec_iters = (int*)d;
-        d += (size_t)2 * W * sizeof(int);
+        d += (size_t)2 * Wd * sizeof(int);
         m->dec_flags = (int*)d;
-        d += (size_t)2 * W * sizeof(int);
+        d += (size_t)2 * Wd * sizeof(int);
         m->dec_remaining = (int*)d;
         // The K padding of the slice buffers is never written: zero it once.
         RGF_CUDA_TRY(cudaMemsetAsync(m->hsa[0], 0,
-                                     2 * sa_bytes(2 * W, b, m->Kp, kSlicesHP) + 2 * sb_bytes(2 * W, b, m->Kp, kSlicesHP),
+                                     2 * sa_bytes(2 * Wd, b, m->Kp, kSlicesHP) + 2 * sb_bytes(2 * Wd, b, m->Kp, kSlicesHP),
                                      st));
     }
     if (cudaMallocHost((void**)&m->h_bad, 2 * sizeof(int)) != cudaSuccess) {

@@ -57,7 +57,7 @@ struct Request {
 
 struct Engine {
     Server* sv = nullptr;
-    int bc = 0, W = 0;
+    int bc = 0, W = 0, Wd = 0;  // slots, decimation batch
     cudaStream_t st = nullptr;
     MixedState ms;
     std::thread th;
@@ -137,8 +137,11 @@ rgf_status engine_init(Engine* e) {
     Server* sv = e->sv;
     RGF_CUDA_TRY(cudaStreamCreateWithFlags(&e->st, cudaStreamNonBlocking));
     const int W = e->W;
-    RGF_TRY(mixed_state_init(&e->ms, e->bc, W, nullptr, e->st));
-    e->ws_bytes = mixed_workspace_bytes(W, e->bc) + mixed_dec_bytes(W, e->bc);
+    // Decimation batches of at most 148 items (one per SM): more slots do not
+    // need a larger decimation pool.
+    e->Wd = std::min(W, 148);
+    RGF_TRY(mixed_state_init(&e->ms, e->bc, W, nullptr, e->st, e->Wd, W));
+    e->ws_bytes = mixed_workspace_bytes(W, e->bc, W, std::max(W, 2 * e->Wd)) + mixed_dec_bytes(e->Wd, e->bc);
     auto dal = [&](void** p, size_t n) -> rgf_status {
         if (cudaMalloc(p, n) != cudaSuccess) {
             cudaGetLastError();
@@ -149,15 +152,15 @@ rgf_status engine_init(Engine* e) {
     };
     RGF_TRY(dal((void**)&e->d_tab, sizeof(SlotTab) * W));
     RGF_TRY(dal((void**)&e->d_masks, sizeof(int) * 5 * W));
-    RGF_TRY(dal((void**)&e->d_dtab, sizeof(DecTab) * W));
+    RGF_TRY(dal((void**)&e->d_dtab, sizeof(DecTab) * e->Wd));
     RGF_TRY(dal((void**)&e->slot_T, sizeof(double) * W));
     RGF_TRY(dal((void**)&e->slot_err, sizeof(double) * W));
     RGF_TRY(dal((void**)&e->slot_flags, sizeof(int) * W));
-    RGF_TRY(dal((void**)&e->dec_err, sizeof(double) * W));
-    RGF_TRY(dal((void**)&e->dec_flags, sizeof(int) * W));
+    RGF_TRY(dal((void**)&e->dec_err, sizeof(double) * e->Wd));
+    RGF_TRY(dal((void**)&e->dec_flags, sizeof(int) * e->Wd));
     RGF_CUDA_TRY(cudaMallocHost((void**)&e->h_tab, sizeof(SlotTab) * W));
     RGF_CUDA_TRY(cudaMallocHost((void**)&e->h_masks, sizeof(int) * 5 * W));
-    RGF_CUDA_TRY(cudaMallocHost((void**)&e->h_dtab, sizeof(DecTab) * W));
+    RGF_CUDA_TRY(cudaMallocHost((void**)&e->h_dtab, sizeof(DecTab) * e->Wd));
     e->slots.assign(W, Engine::Slot{});
     const char* ng = getenv("RGF_NO_GRAPHS");
     e->graphs = !(ng && ng[0] == '1');
@@ -463,8 +466,8 @@ void engine_loop(Engine* e) {
                 if (!pending_refill) {
                     std::vector<std::pair<Request*, int>> items;
                     for (Request* r : e->reqs) {
-                        while (r->next < r->in.n_E && (int)items.size() < W) items.emplace_back(r, r->next++);
-                        if ((int)items.size() >= W) break;
+                        while (r->next < r->in.n_E && (int)items.size() < e->Wd) items.emplace_back(r, r->next++);
+                        if ((int)items.size() >= e->Wd) break;
                     }
                     rgf_status s = engine_decimate(e, items);
                     if (s != RGF_OK) {

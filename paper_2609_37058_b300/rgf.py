@@ -109,6 +109,10 @@ def lib():
         "rgf_server_stats_get": (ctypes.c_int, [_P, ctypes.POINTER(rgf_server_stats)]),
         "rgf_server_destroy": (ctypes.c_int, [_P]),
         "rgf_server_set_class": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+        "rgf_bloch_sum": (ctypes.c_int, [ctypes.c_int, _P, _P, ctypes.c_int, ctypes.c_int, _P, _P, _P]),
+        "rgf_kmesh_mean": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, _P, _P, _P]),
+        "rgf_current": (ctypes.c_int, [ctypes.c_int, _P, _P, ctypes.c_int, _P, ctypes.c_double, ctypes.c_double,
+                                       _P, _P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -479,6 +483,94 @@ class Server:
 
     def __exit__(self, *a):
         self.close()
+
+
+# ----------------------------------------------------------------- k points (include/rgf_kpoints.h)
+def rgf_bloch_sum(R, k, X_R, X_k, cuda_stream=0):
+    """X_k = sum_r exp(2 pi i k.R_r) X_R[r] for CUDA complex128 tensors
+    X_R (n_R, n_blocks, b, b) and X_k (n_blocks, b, b); R (n_R, 2) ints, k (2,)."""
+    R = np.ascontiguousarray(R, dtype=np.int32)
+    k = np.ascontiguousarray(np.asarray(k, dtype=np.float64).reshape(-1)[:2])
+    pr, mr = _ptr(X_R, np.complex128)
+    pk, mk = _ptr(X_k, np.complex128)
+    if mr != RGF_MEM_DEVICE or mk != RGF_MEM_DEVICE:
+        raise TypeError("rgf_bloch_sum takes device tensors")
+    n_R, n_blocks, b = int(X_R.shape[0]), int(X_R.shape[1]), int(X_R.shape[2])
+    if R.shape != (n_R, 2) or tuple(X_k.shape) != (n_blocks, b, b):
+        raise ValueError("shape mismatch")
+    _check(lib().rgf_bloch_sum(n_R, R.ctypes.data, k.ctypes.data, n_blocks, b, pr, pk,
+                               _P(cuda_stream) if cuda_stream else None), "rgf_bloch_sum")
+
+
+def rgf_kmesh_mean(T_k, w, T, cuda_stream=0):
+    """T = sum_k w[k] T_k[k] for CUDA float64 tensors T_k (n_k, n_E), w (n_k), T (n_E)."""
+    p1, _ = _ptr(T_k, np.float64)
+    p2, _ = _ptr(w, np.float64)
+    p3, _ = _ptr(T, np.float64)
+    _check(lib().rgf_kmesh_mean(int(T_k.shape[0]), int(T_k.shape[1]), p1, p2, p3,
+                                _P(cuda_stream) if cuda_stream else None), "rgf_kmesh_mean")
+
+
+def kpoint_transmission(server, kdev, kpts, weights, E, eta, group=8):
+    """T(E) of a transverse-periodic device averaged over a k mesh, through
+    ``server`` (a ``Server``).  ``kdev`` has R (n_R, 2) and R-resolved block
+    arrays (as synth.devices.KDevice).  The Bloch sums and the mesh average
+    run in the library's kernels; ``group`` k-points are in flight at once.
+    Returns (T (n_E,), T_k (n_k, n_E)) as host arrays."""
+    import types
+
+    import torch
+    stream = torch.cuda.current_stream().cuda_stream
+    up = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.complex128)).cuda()
+    names = ("H_diag", "S_diag", "H_lower", "S_lower")
+    XR = {n: up(getattr(kdev, n)) for n in names}
+    fields = ("H00", "S00", "H10", "S10", "Hc", "Sc")
+    LR = [up(np.stack([getattr(L, f) for f in fields], axis=1)) for L in (kdev.lead_L, kdev.lead_R)]
+    R = np.asarray(kdev.R)
+    N, b = int(XR["H_diag"].shape[1]), int(XR["H_diag"].shape[2])
+    E = np.ascontiguousarray(E, dtype=np.float64)
+    n_k = len(kpts)
+    Tk = torch.empty((n_k, E.shape[0]), dtype=torch.float64, device="cuda")
+    for g0 in range(0, n_k, group):
+        flight = []
+        for ki in range(g0, min(n_k, g0 + group)):
+            blocks = {}
+            for n in names:
+                X = XR[n]
+                if X.shape[1] == 0:
+                    blocks[n] = torch.empty((0, b, b), dtype=torch.complex128, device="cuda")
+                    continue
+                Y = torch.empty(tuple(X.shape[1:]), dtype=torch.complex128, device="cuda")
+                rgf_bloch_sum(R, kpts[ki], X, Y, stream)
+                blocks[n] = Y
+            leads = []
+            for X in LR:
+                Y = torch.empty((6, b, b), dtype=torch.complex128, device="cuda")
+                rgf_bloch_sum(R, kpts[ki], X, Y, stream)
+                leads.append(tuple(Y[i] for i in range(6)))
+            dev = types.SimpleNamespace(lead_L=leads[0], lead_R=leads[1], **blocks)
+            flight.append((ki, server.submit(dev, E, eta), dev))
+        for ki, t, _ in flight:
+            r = server.poll(t, timeout_us=-1)
+            Tk[ki] = torch.from_numpy(r[0]).to("cuda")
+    w = torch.as_tensor(np.asarray(weights, dtype=np.float64)).to("cuda")
+    T = torch.empty(E.shape[0], dtype=torch.float64, device="cuda")
+    rgf_kmesh_mean(Tk, w, T, stream)
+    return T.cpu().numpy(), Tk.cpu().numpy()
+
+
+# ----------------------------------------------------------------- observables (include/rgf_observables.h)
+def rgf_current(E, T, V, E_F, kT, I, cuda_stream=0):
+    """Landauer current I[v] (ampere) for CUDA float64 tensors E, T (n_E),
+    V, I (n_V); energies, biases, E_F and kT in eV."""
+    pe, me = _ptr(E, np.float64)
+    pt, mt = _ptr(T, np.float64)
+    pv, mv = _ptr(V, np.float64)
+    pi, mi = _ptr(I, np.float64)
+    if {me, mt, mv, mi} != {RGF_MEM_DEVICE}:
+        raise TypeError("rgf_current takes device tensors")
+    _check(lib().rgf_current(int(E.shape[0]), pe, pt, int(V.shape[0]), pv, float(E_F), float(kT), pi,
+                             _P(cuda_stream) if cuda_stream else None), "rgf_current")
 
 
 # ----------------------------------------------------------------- convenience

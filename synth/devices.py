@@ -266,3 +266,84 @@ def serving_trace(seed: int, *, rate: float, duration: float, N_lo: int, N_hi: i
         out.append(dict(t=t, N=N, b=b, n_E=n_E, E=energy_grid(c - window, c + window, n_E), eta=eta,
                         seed=int(rng.integers(0, 2**31 - 1))))
     return out
+
+
+@dataclasses.dataclass
+class KDevice:
+    """A device periodic in the transverse directions: every block is given
+    per transverse lattice vector R (integer coordinates, row r of ``R``);
+    leads likewise (each Lead field has shape (n_R, b, b)).  X[r] is the
+    block between the home cell and the cell displaced by R[r]."""
+    R: np.ndarray        # (n_R, 2) int
+    H_diag: np.ndarray   # (n_R, N, b, b)
+    S_diag: np.ndarray
+    H_lower: np.ndarray  # (n_R, N-1, b, b)
+    S_lower: np.ndarray
+    lead_L: Lead
+    lead_R: Lead
+    name: str = ""
+
+    @property
+    def n_layers(self) -> int:
+        return self.H_diag.shape[1]
+
+    @property
+    def b(self) -> int:
+        return self.H_diag.shape[2]
+
+
+def periodic_kdevice(N: int, b: int, seed: int, *, metal_frac: float = 0.25, gap_offset: float = 0.6,
+                     transverse: float = 0.3, name: str = "") -> KDevice:
+    """Junction with one periodic transverse direction, R in {0, +1, -1}.
+
+    R = 0 blocks follow ``random_device`` (same recipe and seed).  The
+    transverse blocks are drawn afterwards from the same generator, in this
+    order: on-site H_ii(+1) entries N(0, transverse/sqrt(b)); S_ii(+1)
+    entries N(0, 0.01 sqrt(8/b)); couplings H_{i,i-1}(+1) and H_{i,i-1}(-1)
+    entries N(0, 0.5 transverse/sqrt(b)); S_{i,i-1}(+1) and S_{i,i-1}(-1)
+    entries N(0, 0.005 sqrt(8/b)).  On-site blocks satisfy X(-1) = X(+1)^dagger
+    (so that H(k) and S(k) are Hermitian).  Leads repeat layer 0 and layer
+    N-1 as in ``periodic_leads``.
+    """
+    d0 = random_device(N, b, seed, metal_frac=metal_frac, gap_offset=gap_offset)
+    rng = np.random.default_rng([seed, 1])
+    Hd1 = _cnormal(rng, (N, b, b), transverse / math.sqrt(b))
+    Sd1 = _cnormal(rng, (N, b, b), 0.01 * math.sqrt(8.0 / b))
+    Hl = [_cnormal(rng, (N - 1, b, b), 0.5 * transverse / math.sqrt(b)) for _ in range(2)]
+    Sl = [_cnormal(rng, (N - 1, b, b), 0.005 * math.sqrt(8.0 / b)) for _ in range(2)]
+    R = np.array([[0, 0], [1, 0], [-1, 0]], dtype=np.int32)
+    H_diag = np.stack([d0.H_diag, Hd1, _dag(Hd1)])
+    S_diag = np.stack([d0.S_diag, Sd1, _dag(Sd1)])
+    H_lower = np.stack([d0.H_lower, Hl[0], Hl[1]])
+    S_lower = np.stack([d0.S_lower, Sl[0], Sl[1]])
+    lead = lambda i, j: Lead(H00=H_diag[:, i].copy(), S00=S_diag[:, i].copy(), H10=H_lower[:, j].copy(),
+                             S10=S_lower[:, j].copy(), Hc=H_lower[:, j].copy(), Sc=S_lower[:, j].copy())
+    return KDevice(R=R, H_diag=np.ascontiguousarray(H_diag), S_diag=np.ascontiguousarray(S_diag),
+                   H_lower=np.ascontiguousarray(H_lower), S_lower=np.ascontiguousarray(S_lower),
+                   lead_L=lead(0, 0), lead_R=lead(N - 1, N - 2), name=name or f"kdev_N{N}_b{b}")
+
+
+def chain_stack(N: int, eps: float = 0.0, t: float = 1.0, ty: float = 0.25) -> KDevice:
+    """Uniform chains (on-site eps, hopping t along transport, S = I) side by
+    side, each coupled to its transverse neighbours by ty: b = 1, R in
+    {0, +1, -1}, H_ii(+-1) = ty.  Leads continue the chains."""
+    R = np.array([[0, 0], [1, 0], [-1, 0]], dtype=np.int32)
+    z = lambda *s: np.zeros(s, dtype=np.complex128)
+    H_diag, S_diag = z(3, N, 1, 1), z(3, N, 1, 1)
+    H_diag[0], H_diag[1], H_diag[2] = eps, ty, ty
+    S_diag[0] = 1.0
+    H_lower, S_lower = z(3, N - 1, 1, 1), z(3, N - 1, 1, 1)
+    H_lower[0] = t
+    lead = lambda: Lead(H00=H_diag[:, 0].copy(), S00=S_diag[:, 0].copy(), H10=H_lower[:, 0].copy(),
+                        S10=S_lower[:, 0].copy(), Hc=H_lower[:, 0].copy(), Sc=S_lower[:, 0].copy())
+    return KDevice(R=R, H_diag=H_diag, S_diag=S_diag, H_lower=H_lower, S_lower=S_lower, lead_L=lead(),
+                   lead_R=lead(), name=f"chain_stack_N{N}")
+
+
+def monkhorst_pack(n1: int, n2: int = 1):
+    """Monkhorst-Pack mesh: k_i = (2 m - n_i - 1) / (2 n_i), m = 1..n_i,
+    equal weights.  Returns (k (n, 2), w (n,))."""
+    k1 = (2.0 * np.arange(1, n1 + 1) - n1 - 1) / (2.0 * n1)
+    k2 = (2.0 * np.arange(1, n2 + 1) - n2 - 1) / (2.0 * n2)
+    k = np.array([[a, b_] for a in k1 for b_ in k2], dtype=np.float64)
+    return k, np.full(k.shape[0], 1.0 / k.shape[0])

@@ -84,3 +84,16 @@ def test_server_defaults_and_invalid_arguments(L):
     assert L.rgf_server_create(ctypes.byref(h), ctypes.byref(bad)) == rgf.RGF_E_INVALID
     assert L.rgf_server_poll(None, 1, None, None, None, None, 0) == rgf.RGF_E_INVALID
     assert L.rgf_server_destroy(None) == rgf.RGF_OK
+
+
+def test_library_has_no_unresolved_internal_symbols(L):
+    # Every symbol of the library's own namespace must be defined in it.
+    import shutil
+    import subprocess
+    nm = shutil.which("nm")
+    if nm is None:
+        pytest.skip("nm not available")
+    out = subprocess.run([nm, "-D", "--undefined-only", rgf.LIB_PATH], capture_output=True, text=True,
+                         check=True).stdout
+    bad = [ln for ln in out.splitlines() if "rgf" in ln]
+    assert not bad, bad

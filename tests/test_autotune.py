@@ -23,8 +23,9 @@ def test_coordinate_search_finds_the_best_on_each_axis():
 
 
 def test_search_keeps_the_start_when_nothing_is_faster():
+    # Equal rates: start tile and panel, and the fewest slots (least memory).
     cfg, rate, _ = autotune.search(lambda bc, c: 1.0, 64)
-    assert cfg == {"tile_n": autotune.TILES[0], "panel": autotune.PANELS[0], "slots": autotune.SLOTS[0]}
+    assert cfg == {"tile_n": autotune.TILES[0], "panel": autotune.PANELS[0], "slots": min(autotune.SLOTS)}
 
 
 def test_tuning_table_round_trip(tmp_path):
@@ -40,3 +41,9 @@ def test_slot_doubling_stops_at_the_cap():
     cfg, rate, log = autotune.search(lambda bc, c: float(c["slots"]), 64)
     assert cfg["slots"] == autotune.MAX_SLOTS
     assert max(c["slots"] for c in log) == autotune.MAX_SLOTS
+
+
+def test_smallest_slot_count_within_tolerance_is_kept():
+    rates = {74: 0.8, 148: 1.0, 296: 1.10, 592: 1.14, 1184: 1.16}
+    cfg, rate, _ = autotune.search(lambda bc, c: rates[c["slots"]], 256)
+    assert cfg["slots"] == 592 and rate == 1.14  # 1.14 >= 0.97 * 1.16

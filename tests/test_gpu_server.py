@@ -7,7 +7,7 @@ mix of others is compared, and admission by resident bytes is exercised.
 import numpy as np
 import pytest
 
-from helpers import MIXED_ABS
+from helpers import MIXED_ABS, fp64_uncertainty
 from oracle import rgf_oracle as o
 from synth import Lead, random_device
 from synth.devices import Device, energy_grid, uneven_batch
@@ -138,12 +138,15 @@ def test_class_settings_give_the_same_result(rgf):
     dev = random_device(8, 64, 9, metal_frac=0.25, gap_offset=0.6)
     E = energy_grid(-1.5, 1.5, 10)
     T_o = o.transmission(dev, E, 1e-6)
+    # At E = 0.5 the FP64 oracle's own rounding sensitivity (its spread over
+    # exact gauge transformations) is 8e-7: the bar there is 4x that spread.
+    bar = np.maximum(MIXED_ABS, 4.0 * fp64_uncertainty(dev, E, 1e-6, T_o, n_gauges=2))
     base = None
     for tile_n in (64, 80, 96):
         for panel in (16, 32):
             (r,), _ = serve(rgf, [(dev, E, 1e-6)], slots=8, class_step=32,
                             tuning={64: {"slots": 8, "tile_n": tile_n, "panel": panel}})
-            assert np.abs(r[0] - T_o).max() <= MIXED_ABS, (tile_n, panel)
+            assert np.all(np.abs(r[0] - T_o) <= bar), (tile_n, panel)
             if base is None:
                 base = r[0]
             assert np.abs(r[0] - base).max() <= 1e-10, (tile_n, panel)
