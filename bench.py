@@ -41,7 +41,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
-    ap.add_argument("--wave", type=int, default=148, help="energies per step and rank")
+    ap.add_argument("--wave", type=int, default=296, help="energies per step and rank (two per SM)")
     ap.add_argument("--fp64-wave", type=int, default=16, help="energies of the FP64 GPU comparison step")
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 GPU comparison step")
     ap.add_argument("--cpu-energies", type=int, default=2, help="energies of the oracle CPU sample")
@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=30.0, help="arrival window of the serving run (0 skips it)")
     ap.add_argument("--serve-rate", type=float, default=1.0, help="Poisson arrival rate of the serving run (1/s)")
     ap.add_argument("--serve-energies", default="32,128", help="energy-window sizes of serving requests (lo,hi)")
+    ap.add_argument("--kpoints", type=int, default=8, help="k-points of the transverse-mesh run (0 skips it)")
+    ap.add_argument("--ldos-energies", type=int, default=148, help="energies of the layer-DOS run (0 skips it)")
     return ap.parse_args()
 
 
@@ -187,7 +189,7 @@ def run_batched(args, rgf):
     E = np.linspace(-2.0, 2.0, nE)
     eta = 1e-5
     torch.cuda.synchronize()
-    with rgf.Server(slots=148, class_step=32) as sv:
+    with rgf.Server(slots=148, class_step=32, tuning="default") as sv:
         t0 = time.perf_counter()
         tickets = [sv.submit(d, E, eta) for d in devs]
         res = [sv.poll(t, timeout_us=1_800_000_000) for t in tickets]
@@ -225,7 +227,7 @@ def run_serving(args, rgf):
                           b_hi=288, nE_lo=lo, nE_hi=hi)
     devs = [random_device_gpu(r["N"], r["b"], r["seed"], metal_frac=0.25, gap_offset=0.6) for r in trace]
     torch.cuda.synchronize()
-    with rgf.Server(slots=148, class_step=32) as sv:
+    with rgf.Server(slots=148, class_step=32, tuning="default") as sv:
         tickets = []
         t0 = time.perf_counter()
         for r, d in zip(trace, devs):
@@ -249,6 +251,47 @@ def run_serving(args, rgf):
             "engines": st["engines"], "peak_resident_bytes": st["peak_resident_bytes"],
             "capacity_note": "admission capped at min(150 GB, 55% of free device memory)",
             "offered_sweep_tflop_per_s": work / args.serve_seconds / 1e12 if args.serve_seconds else None}
+
+
+def run_kpoints(args, rgf):
+    """Transverse-periodic junction (R in {0, +1, -1}, 64 layers, b = 128)
+    on an n x 1 Monkhorst-Pack mesh, 64 energies per k-point: Bloch sums,
+    one server request per k-point and the mesh average, all on the GPU."""
+    import numpy as np
+
+    from synth.devices import monkhorst_pack, periodic_kdevice
+
+    kd = periodic_kdevice(64, 128, 5)
+    k, w = monkhorst_pack(args.kpoints)
+    E = np.linspace(-1.5, 1.5, 64)
+    with rgf.Server(slots=148, class_step=32, tuning="default") as sv:
+        rgf.kpoint_transmission(sv, kd, k[:1], w[:1], E[:4], 1e-5)  # warm-up: engine creation
+        t0 = time.perf_counter()
+        T, Tk = rgf.kpoint_transmission(sv, kd, k, w, E, 1e-5, group=args.kpoints)
+        dt = time.perf_counter() - t0
+    return {"workload": "periodic_junction_N64_b128", "kpoints": int(len(k)), "energies": int(len(E)),
+            "seconds": dt, "value": len(k) * len(E) / dt, "unit": "energy-k-points/s",
+            "T_mean_range": [float(T.min()), float(T.max())]}
+
+
+def run_ldos(args, rgf):
+    """Layer-resolved DOS of the 200-layer b = 128 junction at n energies
+    (mixed plan: forward sweep keeping every g_i, backward recursion)."""
+    import numpy as np
+
+    from synth import make_workload
+
+    dev, E_all, eta = make_workload("junction_N200_b128")
+    E = np.ascontiguousarray(E_all[: args.ldos_energies])
+    with rgf.Plan(dev.n_layers, dev.b, precision=rgf.RGF_MIXED, eta=eta) as p:
+        p.set_device(dev)
+        p.ldos(E[:2])  # warm-up
+        t0 = time.perf_counter()
+        D = p.ldos(E)
+        dt = time.perf_counter() - t0
+    return {"workload": "junction_N200_b128", "energies": int(len(E)), "layers": dev.n_layers,
+            "seconds": dt, "value": len(E) / dt, "unit": "energy-points/s (all layers)",
+            "D_range": [float(D.min()), float(D.max())]}
 
 
 def main():
@@ -430,6 +473,10 @@ def main():
         line["batched"] = run_batched(args, rgf)
     if args.serve_seconds > 0:
         line["serving"] = run_serving(args, rgf)
+    if args.kpoints > 0:
+        line["kpoints"] = run_kpoints(args, rgf)
+    if args.ldos_energies > 0:
+        line["ldos"] = run_ldos(args, rgf)
     print(json.dumps(line), flush=True)
 
 

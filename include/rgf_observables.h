@@ -28,6 +28,26 @@ extern "C" {
 rgf_status rgf_current(int n_E, const double* E, const double* T, int n_V, const double* V, double E_F, double kT,
                        double* I, void* cuda_stream);
 
+/* Layer-resolved density of states of a mixed-precision plan (blocks and
+ * leads set):
+ *
+ *   D[k][i] = -(1/pi) Im Tr[(G S)_ii],  (G S)_ii = sum_j G_ij S_ji,
+ *
+ * the Mulliken partition of the device DOS over the principal layers, with G
+ * the retarded device Green's function at z = E_k + i eta (lead self-energies
+ * included) and j over the device layers.  The paper shows spatially
+ * resolved LDOS of its finite-bias runs without a formula; this is the
+ * reading used here.  Computed with a forward sweep that keeps every
+ * left-connected g_i and the backward recursion
+ *   G_ii = g_i + g_i M_{i,i+1} G_{i+1,i+1} M_{i+1,i} g_i,
+ *   G_{i,i+1} = -g_i M_{i,i+1} G_{i+1,i+1},  G_{i+1,i} = -G_{i+1,i+1} M_{i+1,i} g_i,
+ * in the mixed-precision arithmetic of RGF_MIXED.  E (n_E) and D (n_E x
+ * n_layers, row-major) are in memory space `mem`.  The call allocates the
+ * stored inverses (n_layers x b x b double-float per energy of a wave) and
+ * shrinks the wave to fit 60% of free memory; RGF_E_OOM if one energy does
+ * not fit, RGF_E_STATE for an FP64 plan or missing blocks. */
+rgf_status rgf_ldos(rgf_plan_t plan, const double* E, int n_E, double* D, int mem);
+
 #ifdef __cplusplus
 }
 #endif

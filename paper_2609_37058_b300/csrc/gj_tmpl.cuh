@@ -222,10 +222,10 @@ __device__ __forceinline__ T2 shfl_c(T2 v, int src) {
 // rows w, w + 8, ...  The panel lives in shared memory with a row pitch of
 // NB + 1 elements; the pivot column is copied to a separate array (fcol) so
 // that the rank-1 update reads and writes never alias and can be pipelined.
-// One pivot step costs two block barriers: the pivot search of the next
-// column is folded into the update (the lane that owns that column tracks
-// its warp's largest candidate), and warp 0 swaps and scales the pivot row
-// while the other warps copy their part of the pivot column.
+// One pivot step: all threads merge the warps' pivot candidates; warp 0
+// swaps and scales the pivot row while the other warps copy their part of
+// the pivot column; barrier; rank-1 update without branches between lanes;
+// barrier; search of the next column by all 256 threads; barrier.
 constexpr int GJ_WARPS = 8;
 template <typename T2, int NB>
 __global__ void __launch_bounds__(256) k_gj_panel(int b, int k0, int nbk, T2* A, long sA, T2* Pbar, int* piv,
@@ -297,35 +297,40 @@ __global__ void __launch_bounds__(256) k_gj_panel(int b, int k0, int nbk, T2* A,
         __syncthreads();
         const T2 pj = col_ok ? pan[j * P + lane] : zero;
         const T2 inv_d = pan[j * P + jj];
-        const bool next = jj + 1 < nbk;
-        const bool track = next && lane == jj + 1;
-        R bv = -1;
-        int bix = b;
         if (col_ok) {
+            // Branch-free over lanes: lane jj takes -f / pivot, the others
+            // x - f p_j.
+            const T2 mid = C::make(-inv_d.x, -inv_d.y);
 #pragma unroll 4
             for (int r = wid; r < b; r += NW) {
-                if (r == j) continue;
                 const T2 f = fcol[r];
-                if (lane == jj) {
-                    pan[r * P + lane] = cmul(C::make(-f.x, -f.y), inv_d);
-                } else {
-                    T2 y = pan[r * P + lane];
-                    y.x -= f.x * pj.x - f.y * pj.y;
-                    y.y -= f.x * pj.y + f.y * pj.x;
-                    pan[r * P + lane] = y;
-                    if (track && r > j) argmax_merge<R>(bv, bix, cabs2(y), r);
-                }
-            }
-        }
-        if (next) {
-            const R v2 = __shfl_sync(0xffffffffu, bv, jj + 1);
-            const int i2 = __shfl_sync(0xffffffffu, bix, jj + 1);
-            if (lane == 0) {
-                red_v[buf ^ 1][wid] = v2;
-                red_i[buf ^ 1][wid] = i2;
+                const T2 x = pan[r * P + lane];
+                T2 y;
+                y.x = x.x - (f.x * pj.x - f.y * pj.y);
+                y.y = x.y - (f.x * pj.y + f.y * pj.x);
+                const T2 out = (lane == jj) ? cmul(f, mid) : y;
+                if (r != j) pan[r * P + lane] = out;
             }
         }
         __syncthreads();
+        if (jj + 1 < nbk) {
+            // Candidates of the next column: rows j+1 .. b-1.
+            const int c = jj + 1;
+            R bv = -1;
+            int bix = b;
+            for (int r = j + 1 + tid; r < b; r += 32 * NW) argmax_merge<R>(bv, bix, cabs2(pan[r * P + c]), r);
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                const R ov = __shfl_down_sync(0xffffffffu, bv, off);
+                const int oi = __shfl_down_sync(0xffffffffu, bix, off);
+                argmax_merge<R>(bv, bix, ov, oi);
+            }
+            if (lane == 0) {
+                red_v[buf ^ 1][wid] = bv;
+                red_i[buf ^ 1][wid] = bix;
+            }
+            __syncthreads();
+        }
     }
     T2* Pb = Pbar + (long)bi * b * nbk;
     if (col_ok) {
@@ -338,28 +343,71 @@ __global__ void __launch_bounds__(256) k_gj_panel(int b, int k0, int nbk, T2* A,
     }
 }
 
+// Row interchanges of one panel applied to the other columns, and T = rows
+// K of those columns after the interchanges.  A CTA owns 32 columns of one
+// matrix: it stages the (at most 2 nb) rows that the panel's interchanges
+// touch in shared memory, applies the interchanges there, and writes the
+// rows back, so the global accesses are coalesced and independent.
 template <typename T2>
-__global__ void k_gj_swap(int b, int k0, int nbk, T2* A, long sA, const int* piv, T2* T, const int* active) {
+__global__ void __launch_bounds__(256) k_gj_swap(int b, int k0, int nbk, T2* A, long sA, const int* piv, T2* T,
+                                                 const int* active) {
     const int bi = blockIdx.y;
     if (active && !active[bi]) return;
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= b) return;
+    __shared__ int rows[64];
+    __shared__ int slot_p[32];
+    __shared__ int n_rows;
+    __shared__ T2 tile[64][33];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int c = blockIdx.x * 32 + lane;
     T2* Ab = A + (long)bi * sA;
     T2* Tb = T + (long)bi * nbk * b;
     const int* pv = piv + (long)bi * b;
-    if (c >= k0 && c < k0 + nbk) {
-        for (int jj = 0; jj < nbk; ++jj) Tb[(long)jj * b + c] = CT<T2>::make(0, 0);
-        return;
+    if (tid == 0) {
+        // Slots 0..nbk-1 are rows k0..k0+nbk-1; pivot rows beyond the panel
+        // get the next slots (each once).
+        int n = nbk;
+        for (int jj = 0; jj < nbk; ++jj) rows[jj] = k0 + jj;
+        for (int jj = 0; jj < nbk; ++jj) {
+            const int p = pv[k0 + jj];
+            int sp = -1;
+            if (p < k0 + nbk) {
+                sp = p - k0;
+            } else {
+                for (int q = nbk; q < n; ++q)
+                    if (rows[q] == p) sp = q;
+                if (sp < 0) {
+                    sp = n;
+                    rows[n++] = p;
+                }
+            }
+            slot_p[jj] = sp;
+        }
+        n_rows = n;
     }
-    for (int jj = 0; jj < nbk; ++jj) {
-        const int j = k0 + jj, p = pv[j];
-        if (p != j) {
-            T2 t = Ab[(long)j * b + c];
-            Ab[(long)j * b + c] = Ab[(long)p * b + c];
-            Ab[(long)p * b + c] = t;
+    __syncthreads();
+    const int n = n_rows;
+    const bool in_panel = c >= k0 && c < k0 + nbk;
+    const bool ok = c < b && !in_panel;
+    for (int q = wid; q < n; q += 8) tile[q][lane] = ok ? Ab[(long)rows[q] * b + c] : CT<T2>::make(0, 0);
+    __syncthreads();
+    if (wid == 0 && ok) {
+        for (int jj = 0; jj < nbk; ++jj) {
+            const int sp = slot_p[jj];
+            if (sp != jj) {
+                const T2 t = tile[jj][lane];
+                tile[jj][lane] = tile[sp][lane];
+                tile[sp][lane] = t;
+            }
         }
     }
-    for (int jj = 0; jj < nbk; ++jj) Tb[(long)jj * b + c] = Ab[(long)(k0 + jj) * b + c];
+    __syncthreads();
+    if (c >= b) return;
+    if (in_panel) {
+        for (int jj = wid; jj < nbk; jj += 8) Tb[(long)jj * b + c] = CT<T2>::make(0, 0);
+        return;
+    }
+    for (int q = wid; q < n; q += 8) Ab[(long)rows[q] * b + c] = tile[q][lane];
+    for (int jj = wid; jj < nbk; jj += 8) Tb[(long)jj * b + c] = tile[jj][lane];
 }
 
 // Undo the column interchanges: column c of the result is stored column
@@ -436,8 +484,8 @@ rgf_status inv_t(int batch, int b, T2* A, long sA, void* ws, int* flags, const i
         panel<<<batch, 256, sm, st>>>(b, k0, nbk, A, sA, Pbar, piv, flags, active);
         RGF_LAUNCH_CHECK();
         if (nbk < b) {
-            dim3 g2(ceil_div(b, 128), batch);
-            k_gj_swap<T2><<<g2, 128, 0, st>>>(b, k0, nbk, A, sA, piv, T, active);
+            dim3 g2(ceil_div(b, 32), batch);
+            k_gj_swap<T2><<<g2, 256, 0, st>>>(b, k0, nbk, A, sA, piv, T, active);
             RGF_LAUNCH_CHECK();
             if constexpr (std::is_same<T2, float2>::value) {
                 RGF_TRY(gj_update_f32(batch, b, b, nbk, Pbar, (long)b * nbk, T, (long)nbk * b, A, b, sA, k0,

@@ -112,4 +112,23 @@ inline double2* dec_unit(const MixedState* m, int W, int u) { return m->dec_pool
 // NOCONV and SINGULAR bits.
 rgf_status hp_decimate_run(const Ctx& c, int W, double tol, int max_iter, double2** g_out);
 
+// Device Hamiltonian of a mixed-precision plan in double-float, plus its
+// workspace (rgf_plan_s::mixed).
+struct PlanMixed {
+    MixedState ms;
+    float4* H_diag = nullptr;
+    float4* S_diag = nullptr;
+    float4* H_lower = nullptr;
+    float4* S_lower = nullptr;
+    float4* lead[2][6] = {};
+};
+
+}  // namespace rgf
+
+struct rgf_plan_s;
+namespace rgf {
+// Lead decimation, Sigma and Gamma of a plan's W energies (p->d_E) into pool
+// units 0 (Sigma_L, Sigma_R) and 2 (Gamma_L, Gamma_R); resets p->d_flags and
+// p->d_err.
+rgf_status mixed_leads(rgf_plan_s* p, int W, const Ctx& c);
 }  // namespace rgf

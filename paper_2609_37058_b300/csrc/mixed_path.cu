@@ -16,15 +16,6 @@
 namespace rgf {
 
 namespace {
-// Device Hamiltonian of a plan in double-float, plus its workspace.
-struct PlanMixed {
-    MixedState ms;
-    float4* H_diag = nullptr;
-    float4* S_diag = nullptr;
-    float4* H_lower = nullptr;
-    float4* S_lower = nullptr;
-    float4* lead[2][6] = {};
-};
 
 size_t sa_bytes(int cnt, int b, int Kp, int nsl = kSlices) {
     return (size_t)cnt * nsl * b * Kp * sizeof(__nv_bfloat16);
@@ -420,15 +411,17 @@ rgf_status mixed_on_lead(rgf_plan_s* p, int side) {
     return RGF_OK;
 }
 
-rgf_status mixed_wave(rgf_plan_s* p, int W) {
+// Decimation of both leads, self-energies and broadening matrices for the
+// W energies in p->d_E: Sigma_L, Sigma_R in pool unit 0 (2W entries),
+// Gamma_L, Gamma_R in unit 2.  Clears and fills p->d_flags / p->d_err.
+rgf_status mixed_leads(rgf_plan_s* p, int W, const Ctx& c) {
     auto* pm = (PlanMixed*)p->mixed;
     MixedState* m = &pm->ms;
     cudaStream_t st = p->stream;
-    const int b = p->b, N = p->N;
+    const int b = p->b;
     const long nn = (long)b * b;
     const double eta = p->opt.eta;
     const double* E = p->d_E;
-    Ctx c{m, st, nn, b, p->opt.ns_steps, p->d_err, p->d_flags, &p->n_reseeds};
     auto U = [&](int unit) { return m->pool + (long)unit * W * nn; };
     const int W2 = 2 * W;
 
@@ -463,19 +456,33 @@ rgf_status mixed_wave(rgf_plan_s* p, int W) {
     // ---------------------------------------------------------- self-energies
     float4* sigma = U(0);
     float4* gamma = U(2);
-    {
-        FormSrcDf x1{{L[5], Rl[5]}, {L[4], Rl[4]}, {0, 1}};
-        FormSrcDf x2{{L[5], Rl[5]}, {L[4], Rl[4]}, {1, 0}};
-        RGF_TRY(form_dfc(W, 2, b, E, eta, x1, t1, nullptr, nullptr, st));
-        RGF_TRY(form_dfc(W, 2, b, E, eta, x2, t2, nullptr, nullptr, st));
-        RGF_TRY(sliceA(c, W2, 0, t1, nullptr));
-        RGF_TRY(sliceB(c, W2, 0, g, nullptr));
-        RGF_TRY(mm(c, W2, 0, 0, 1.0f, nullptr, 0, t3, nullptr));
-        RGF_TRY(sliceA(c, W2, 0, t3, nullptr));
-        RGF_TRY(sliceB(c, W2, 0, t2, nullptr));
-        RGF_TRY(mm(c, W2, 0, 0, 1.0f, nullptr, 0, sigma, nullptr));
-        RGF_TRY(gamma_dfc(W2, b, sigma, gamma, st));
-    }
+    FormSrcDf x1{{L[5], Rl[5]}, {L[4], Rl[4]}, {0, 1}};
+    FormSrcDf x2{{L[5], Rl[5]}, {L[4], Rl[4]}, {1, 0}};
+    RGF_TRY(form_dfc(W, 2, b, E, eta, x1, t1, nullptr, nullptr, st));
+    RGF_TRY(form_dfc(W, 2, b, E, eta, x2, t2, nullptr, nullptr, st));
+    RGF_TRY(sliceA(c, W2, 0, t1, nullptr));
+    RGF_TRY(sliceB(c, W2, 0, g, nullptr));
+    RGF_TRY(mm(c, W2, 0, 0, 1.0f, nullptr, 0, t3, nullptr));
+    RGF_TRY(sliceA(c, W2, 0, t3, nullptr));
+    RGF_TRY(sliceB(c, W2, 0, t2, nullptr));
+    RGF_TRY(mm(c, W2, 0, 0, 1.0f, nullptr, 0, sigma, nullptr));
+    RGF_TRY(gamma_dfc(W2, b, sigma, gamma, st));
+    return RGF_OK;
+}
+
+rgf_status mixed_wave(rgf_plan_s* p, int W) {
+    auto* pm = (PlanMixed*)p->mixed;
+    MixedState* m = &pm->ms;
+    cudaStream_t st = p->stream;
+    const int b = p->b, N = p->N;
+    const long nn = (long)b * b;
+    const double eta = p->opt.eta;
+    const double* E = p->d_E;
+    Ctx c{m, st, nn, b, p->opt.ns_steps, p->d_err, p->d_flags, &p->n_reseeds};
+    auto U = [&](int unit) { return m->pool + (long)unit * W * nn; };
+    RGF_TRY(mixed_leads(p, W, c));
+    float4* sigma = U(0);
+    float4* gamma = U(2);
     float4* sigL = sigma;
     float4* sigR = sigma + (long)W * nn;
     float4* gamL = gamma;

@@ -113,6 +113,7 @@ def lib():
         "rgf_kmesh_mean": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, _P, _P, _P]),
         "rgf_current": (ctypes.c_int, [ctypes.c_int, _P, _P, ctypes.c_int, _P, ctypes.c_double, ctypes.c_double,
                                        _P, _P]),
+        "rgf_ldos": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, ctypes.c_int]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -573,6 +574,14 @@ def rgf_current(E, T, V, E_F, kT, I, cuda_stream=0):
                              _P(cuda_stream) if cuda_stream else None), "rgf_current")
 
 
+def rgf_ldos(plan, E, D):
+    """Layer DOS D (n_E, n_layers) of a mixed plan at energies E (host
+    numpy arrays or CUDA tensors, both in the same memory space)."""
+    pe, me = _ptr(E, np.float64)
+    pd, md = _ptr(D, np.float64)
+    _check(lib().rgf_ldos(plan, pe, int(E.shape[0]), pd, _mem_of((pe, me), (pd, md))), "rgf_ldos")
+
+
 # ----------------------------------------------------------------- convenience
 class Plan:
     """Owns one rgf_plan_t.  ``precision`` is RGF_FP64 or RGF_MIXED."""
@@ -603,6 +612,13 @@ class Plan:
         flags = np.empty(E.shape[0], dtype=np.int32)
         rgf_transmission(self.handle, E, T, err, flags)
         return T, err, flags
+
+    def ldos(self, E):
+        """Layer-resolved DOS (n_E, n_layers) of a RGF_MIXED plan."""
+        E = np.ascontiguousarray(E, dtype=np.float64)
+        D = np.empty((E.shape[0], self.n_layers))
+        rgf_ldos(self.handle, E, D)
+        return D
 
     @property
     def stats(self):

@@ -49,3 +49,33 @@ def test_current_from_the_mixed_path(rgf):
     I = gpu_current(rgf, E, T, V, 0.0, 0.01)
     I_o = ob.current(E, T_o, V, 0.0, 0.01)
     assert np.all(np.abs(I - I_o) <= ob.G0 * 1e-6 * (V + 0.1))
+
+
+def test_ldos_matches_oracle(rgf):
+    dev = random_device(7, 12, 8, metal_frac=0.3, gap_offset=0.6)
+    E = np.linspace(-1.2, 1.2, 11)
+    eta = 1e-4
+    with rgf.Plan(dev.n_layers, dev.b, precision=rgf.RGF_MIXED, eta=eta) as p:
+        p.set_device(dev)
+        D = p.ldos(E)
+    D_o = ob.ldos(dev, E, eta)
+    assert np.all(np.abs(D - D_o) <= 1e-6 * np.maximum(1.0, np.abs(D_o))), np.abs(D - D_o).max()
+
+
+def test_ldos_of_a_chain_window(rgf):
+    from synth import chain_device
+    dev = chain_device(9)
+    E = np.array([-1.5, -0.3, 0.8, 1.7])
+    with rgf.Plan(dev.n_layers, dev.b, precision=rgf.RGF_MIXED, eta=1e-6) as p:
+        p.set_device(dev)
+        D = p.ldos(E)
+    assert np.abs(D - ob.ldos(dev, E, 1e-6)).max() <= 1e-6
+
+
+def test_ldos_needs_a_mixed_plan(rgf):
+    dev = random_device(3, 4, 1)
+    with rgf.Plan(dev.n_layers, dev.b, precision=rgf.RGF_FP64, eta=1e-5) as p:
+        p.set_device(dev)
+        with pytest.raises(rgf.RGFError) as ex:
+            p.ldos(np.array([0.1]))
+        assert ex.value.status == rgf.RGF_E_STATE
