@@ -17,8 +17,11 @@
  *     energy) item through the sweep at its own layer, and a slot whose
  *     device is finished is refilled from the next lead-decimated items, so
  *     devices of different lengths share every launch (continuous batching);
- *   - lead decimation and self-energies run for `slots` items at a time,
+ *   - lead decimation and self-energies run for up to 148 items at a time,
  *     ahead of the slots that take them;
+ *   - from its third step on, an engine replays its step as a captured CUDA
+ *     graph (every kernel of the step launched, masks select the entries;
+ *     RGF_NO_GRAPHS=1 in the environment launches the kernels directly);
  *   - requests are admitted in arrival order while their resident bytes
  *     (device blocks in double-float, FP64 lead blocks, energies and
  *     results) fit under capacity_bytes; a request that can never fit is

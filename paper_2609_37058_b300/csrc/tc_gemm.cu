@@ -16,6 +16,7 @@
 // Every wait on an mbarrier is bounded (2 s); a timeout sets a status bit
 // that the host turns into an error, and the CTA still releases its TMEM.
 #include <atomic>
+#include <cstdlib>
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -26,25 +27,34 @@
 namespace rgf {
 
 namespace {
-constexpr int TC_BM = 128, TC_BK = 32;  // BK in BF16 elements (64 bytes)
-constexpr int TC_STAGES = 2;
+constexpr int TC_BM = 128;
 constexpr uint32_t TC_TMEM_COLS = 512;
 
 // Tile configuration of one kernel variant: NSL slices per operand, NGRP
 // TMEM accumulators (groups 0..NGRP-2 exact, the last one the tail), BN real
-// output columns per CTA (NGRP * BN <= 512 TMEM columns).
-template <int NSL, int NGRP, int BN>
+// output columns per CTA (NGRP * BN <= 512 TMEM columns), BK BF16 elements
+// of K per pipeline stage: 32 (64-byte rows, 64-byte swizzle, two stages)
+// or 16 (32-byte rows, 32-byte swizzle, four stages of half the size).
+template <int NSL, int NGRP, int BN, int BK>
 struct TcCfg {
-    static constexpr int ATILE = TC_BM * TC_BK * 2;        // 8 KB per A slice tile
-    static constexpr int BTILE = BN * TC_BK * 2;           // BN rows of 64 bytes
+    static constexpr int STAGES = BK == 32 ? 2 : 4;
+    static constexpr int ATILE = TC_BM * BK * 2;   // A slice tile
+    static constexpr int BTILE = BN * BK * 2;      // BN rows of 2 BK bytes
     static constexpr int STAGE = NSL * (ATILE + BTILE);
-    static constexpr int SMEM = TC_STAGES * STAGE + 1024 + 256;
+    static constexpr int SMEM = STAGES * STAGE + 1024 + 256;
     // Instruction descriptor: D = F32, A = B = BF16, both K-major, N = BN, M = 128.
     static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
                                       ((uint32_t)(TC_BM >> 4) << 24);
+    // Shared-memory descriptor: layout type (4 = 64-byte swizzle, 6 = 32-byte
+    // swizzle) and the byte distance between 8-row groups.
+    static constexpr uint64_t SWZ = BK == 32 ? 4 : 6;
+    static constexpr uint32_t SBO = 8 * BK * 2;
+    static_assert(BK == 16 || BK == 32, "K per stage is 16 or 32 BF16 elements");
     static_assert(NGRP * BN <= 512, "accumulators exceed TMEM");
     static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "invalid N for M = 128");
-    static_assert(BTILE % 1024 == 0, "B tiles must keep 1024-byte alignment");
+    // Tiles start on their swizzle atom (8 rows): 1024 bytes kept for the
+    // 64-byte swizzle, 256 bytes (one atom) for the 32-byte swizzle.
+    static_assert(BTILE % (BK == 32 ? 1024 : 256) == 0, "B tiles must keep swizzle-atom alignment");
 };
 constexpr unsigned long long TC_WAIT_NS = 2000000000ull;
 
@@ -94,15 +104,15 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
         "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
         : "memory");
 }
-// Shared-memory matrix descriptor: K-major tile, rows of 64 bytes with the
-// 64-byte swizzle, 8-row groups 512 bytes apart.
-__device__ __forceinline__ uint64_t desc_sw64(uint32_t saddr) {
+// Shared-memory matrix descriptor: K-major tile with swizzled rows (layout
+// type swz), 8-row groups sbo bytes apart.
+__device__ __forceinline__ uint64_t desc_sw(uint32_t saddr, uint64_t swz, uint32_t sbo) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)1 << 16;              // leading byte offset (unused for this layout)
-    d |= (uint64_t)(512u >> 4) << 32;    // stride byte offset
+    d |= (uint64_t)1 << 16;              // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(sbo >> 4) << 32;     // stride byte offset
     d |= (uint64_t)1 << 46;              // descriptor version
-    d |= (uint64_t)4 << 61;              // 64-byte swizzle
+    d |= swz << 61;
     return d;
 }
 __device__ __forceinline__ void umma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum) {
@@ -162,25 +172,26 @@ struct TcArgs {
     int skip_first_chunk;
 };
 
-template <int NSL, int NGRP, int BN, bool OUT64>
+template <int NSL, int NGRP, int BN, bool OUT64, int BK>
 __global__ void __launch_bounds__(128, 1)
     k_oz_tc(TcArgs g, const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB) {
-    using Cfg = TcCfg<NSL, NGRP, BN>;
+    using Cfg = TcCfg<NSL, NGRP, BN, BK>;
+    constexpr int S = Cfg::STAGES;
     const int bi = blockIdx.z;
     if (g.active && !g.active[bi]) return;
     extern __shared__ __align__(1024) unsigned char smem_tc[];
     unsigned char* base = (unsigned char*)(((uintptr_t)smem_tc + 1023) & ~(uintptr_t)1023);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(base + TC_STAGES * Cfg::STAGE);
-    // bars[0..1] full, bars[2..3] empty, bars[4] done; slot after them
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 8);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(base + S * Cfg::STAGE);
+    // bars[0..S-1] full, bars[S..2S-1] empty, bars[2S] done; slot after them
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * S + 2);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.y * TC_BM, n0 = blockIdx.x * BN;
-    const int nk = g.Kp / TC_BK;
+    const int nk = g.Kp / BK;
     int* status = g.status;
 
     if (tid == 0) {
-        for (int i = 0; i < 5; ++i) mbar_init(smem_u32(&bars[i]), 1);
+        for (int i = 0; i < 2 * S + 1; ++i) mbar_init(smem_u32(&bars[i]), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
@@ -197,9 +208,9 @@ __global__ void __launch_bounds__(128, 1)
     if (tid == 0) {
         // ---------------- TMA producer
         for (int kc = 0; kc < nk; ++kc) {
-            const int s = kc & 1;
-            if (kc >= TC_STAGES) {
-                if (!mbar_wait(smem_u32(&bars[2 + s]), ((kc >> 1) - 1) & 1, status, 0x1, g.wait_ns)) break;
+            const int s = kc % S;
+            if (kc >= S) {
+                if (!mbar_wait(smem_u32(&bars[S + s]), ((kc / S) - 1) & 1, status, 0x1, g.wait_ns)) break;
             }
             if (kc == 0 && g.skip_first_chunk) continue;
             const uint32_t fb = smem_u32(&bars[s]);
@@ -207,8 +218,8 @@ __global__ void __launch_bounds__(128, 1)
             unsigned char* st = base + s * Cfg::STAGE;
 #pragma unroll
             for (int sl = 0; sl < NSL; ++sl) {
-                tma_load_3d(smem_u32(st + sl * Cfg::ATILE), &tmA, kc * TC_BK, m0, bi * NSL + sl, fb);
-                tma_load_3d(smem_u32(st + NSL * Cfg::ATILE + sl * Cfg::BTILE), &tmB, kc * TC_BK, n0, bi * NSL + sl,
+                tma_load_3d(smem_u32(st + sl * Cfg::ATILE), &tmA, kc * BK, m0, bi * NSL + sl, fb);
+                tma_load_3d(smem_u32(st + NSL * Cfg::ATILE + sl * Cfg::BTILE), &tmB, kc * BK, n0, bi * NSL + sl,
                             fb);
             }
         }
@@ -216,8 +227,8 @@ __global__ void __launch_bounds__(128, 1)
         // ---------------- MMA issuer
         bool ok = true;
         for (int kc = 0; kc < nk && ok; ++kc) {
-            const int s = kc & 1;
-            if (!mbar_wait(smem_u32(&bars[s]), (kc >> 1) & 1, status, 0x2, g.wait_ns)) {
+            const int s = kc % S;
+            if (!mbar_wait(smem_u32(&bars[s]), (kc / S) & 1, status, 0x2, g.wait_ns)) {
                 ok = false;
                 break;
             }
@@ -232,18 +243,18 @@ __global__ void __launch_bounds__(128, 1)
                     if (i + j > NSL - 1) continue;
                     const int grp = (i + j) < (NGRP - 1) ? (i + j) : (NGRP - 1);
 #pragma unroll
-                    for (int kk = 0; kk < TC_BK / 16; ++kk) {
-                        const uint64_t ad = desc_sw64(a0 + i * Cfg::ATILE + kk * 32);
-                        const uint64_t bd = desc_sw64(b0 + j * Cfg::BTILE + kk * 32);
+                    for (int kk = 0; kk < BK / 16; ++kk) {
+                        const uint64_t ad = desc_sw(a0 + i * Cfg::ATILE + kk * 32, Cfg::SWZ, Cfg::SBO);
+                        const uint64_t bd = desc_sw(b0 + j * Cfg::BTILE + kk * 32, Cfg::SWZ, Cfg::SBO);
                         const uint32_t acc = (kc > 0 || (started >> grp) & 1u) ? 1u : 0u;
                         umma(taddr + (uint32_t)(grp * BN), ad, bd, Cfg::IDESC, acc);
                         started |= 1u << grp;
                     }
                 }
             }
-            umma_commit(smem_u32(&bars[2 + s]));
+            umma_commit(smem_u32(&bars[S + s]));
         }
-        umma_commit(smem_u32(&bars[4]));
+        umma_commit(smem_u32(&bars[2 * S]));
     }
     __syncwarp();
 
@@ -251,7 +262,7 @@ __global__ void __launch_bounds__(128, 1)
     // One lane per warp waits; the outcome is made warp-uniform because the
     // TMEM loads below are warp-collective.
     int done_i = 0;
-    if (lane == 0) done_i = mbar_wait(smem_u32(&bars[4]), 0, status, 0x4, g.wait_ns) ? 1 : 0;
+    if (lane == 0) done_i = mbar_wait(smem_u32(&bars[2 * S]), 0, status, 0x4, g.wait_ns) ? 1 : 0;
     const bool done = __shfl_sync(0xffffffffu, done_i, 0) != 0;
     __syncwarp();
     tc_fence_after();
@@ -314,7 +325,7 @@ __global__ void __launch_bounds__(128, 1)
     __syncthreads();
     if (!done && tid == 0) {
         // Drain TMA copies that may still be in flight before the CTA exits.
-        for (int s = 0; s < TC_STAGES; ++s) mbar_wait(smem_u32(&bars[s]), 0, status, 0x8, g.wait_ns);
+        for (int s = 0; s < S; ++s) mbar_wait(smem_u32(&bars[s]), 0, status, 0x8, g.wait_ns);
     }
     __syncthreads();
     if (warp == 1) {
@@ -341,10 +352,10 @@ static PFN_cuTensorMapEncodeTiled_v12000 encoder() {
 }
 
 static rgf_status encode_slices(CUtensorMap* map, const __nv_bfloat16* ptr, int Kp, long rows, long planes,
-                                int box_rows) {
+                                int box_rows, int bk) {
     cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)planes};
     cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)rows * Kp * 2};
-    cuuint32_t box[3] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows, 1};
+    cuuint32_t box[3] = {(cuuint32_t)bk, (cuuint32_t)box_rows, 1};
     cuuint32_t estr[3] = {1, 1, 1};
     PFN_cuTensorMapEncodeTiled_v12000 enc = encoder();
     if (!enc) {
@@ -352,7 +363,8 @@ static rgf_status encode_slices(CUtensorMap* map, const __nv_bfloat16* ptr, int 
         return RGF_E_CUDA;
     }
     CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)ptr, dims, strides, box, estr,
-                                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                                        CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                        bk == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B,
                                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
@@ -361,11 +373,11 @@ static rgf_status encode_slices(CUtensorMap* map, const __nv_bfloat16* ptr, int 
     return RGF_OK;
 }
 
-template <int NSL, int NGRP, int BN, bool OUT64>
+template <int NSL, int NGRP, int BN, bool OUT64, int BK>
 static rgf_status launch_tc(const TcArgs& g, cudaStream_t st) {
-    using Cfg = TcCfg<NSL, NGRP, BN>;
+    using Cfg = TcCfg<NSL, NGRP, BN, BK>;
     if (g.batch <= 0) return RGF_OK;
-    if (g.Kp % TC_BK != 0 || ((uintptr_t)g.As & 15) || ((uintptr_t)g.Bs & 15) || !g.status) {
+    if (g.Kp % BK != 0 || ((uintptr_t)g.As & 15) || ((uintptr_t)g.Bs & 15) || !g.status) {
         set_error("oz_gemm_tc: bad slice layout");
         return RGF_E_INVALID;
     }
@@ -374,13 +386,13 @@ static rgf_status launch_tc(const TcArgs& g, cudaStream_t st) {
         return RGF_E_INVALID;
     }
     CUtensorMap ta, tb;
-    RGF_TRY(encode_slices(&ta, g.As, g.Kp, g.m, (long)g.batch * NSL, TC_BM));
-    RGF_TRY(encode_slices(&tb, g.Bs, g.Kp, 2L * g.n, (long)g.batch * NSL, BN));
+    RGF_TRY(encode_slices(&ta, g.As, g.Kp, g.m, (long)g.batch * NSL, TC_BM, BK));
+    RGF_TRY(encode_slices(&tb, g.Bs, g.Kp, 2L * g.n, (long)g.batch * NSL, BN, BK));
     static std::atomic<bool> attr{false};
     if (!attr.load()) {
         // Idempotent: threads that race here all set the same value.
-        RGF_CUDA_TRY(cudaFuncSetAttribute(k_oz_tc<NSL, NGRP, BN, OUT64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          Cfg::SMEM));
+        RGF_CUDA_TRY(cudaFuncSetAttribute(k_oz_tc<NSL, NGRP, BN, OUT64, BK>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM));
         attr.store(true);
     }
     dim3 grid(ceil_div(2L * g.n, BN), ceil_div(g.m, TC_BM), g.batch);
@@ -388,7 +400,7 @@ static rgf_status launch_tc(const TcArgs& g, cudaStream_t st) {
     const bool timed = gemm_timing_enabled() && g.active == nullptr;
     cudaEvent_t ev = nullptr;
     if (timed) gemm_timing_before(st, &ev);
-    k_oz_tc<NSL, NGRP, BN, OUT64><<<grid, 128, Cfg::SMEM, st>>>(g, ta, tb);
+    k_oz_tc<NSL, NGRP, BN, OUT64, BK><<<grid, 128, Cfg::SMEM, st>>>(g, ta, tb);
     RGF_LAUNCH_CHECK();
     if (timed) {
         // NSL(NSL+1)/2 slice-pair real products of M = m, N = 2n, K = 2k per batch entry.
@@ -398,6 +410,16 @@ static rgf_status launch_tc(const TcArgs& g, cudaStream_t st) {
     return RGF_OK;
 }
 
+// K per pipeline stage of the tensor-core cores: 32 (default) or 16 with
+// RGF_TC_BK=16 in the environment (read once).
+static int tc_bk() {
+    static const int bk = [] {
+        const char* e = getenv("RGF_TC_BK");
+        return (e && e[0] == '1' && e[1] == '6') ? 16 : 32;
+    }();
+    return bk;
+}
+
 rgf_status oz_gemm_tc(const OzGemm& g, cudaStream_t st) {
     TcArgs a{g.batch, g.m, g.n, g.k, g.As, g.Bs, g.Kp, g.alpha, g.D, g.sD, g.add_identity, g.C, g.sC, g.active,
              g.status, TC_WAIT_NS, 0};
@@ -405,21 +427,32 @@ rgf_status oz_gemm_tc(const OzGemm& g, cudaStream_t st) {
         a.wait_ns = g.test_wait_ns;
         a.skip_first_chunk = 1;
     }
-    switch (g.bn) {
-        case 64: return launch_tc<kSlices, kGroups, 64, false>(a, st);
-        case 80: return launch_tc<kSlices, kGroups, 80, false>(a, st);
-        case 0:
-        case 96: return launch_tc<kSlices, kGroups, 96, false>(a, st);
-        default:
-            set_error("oz_gemm_tc: unsupported tile width %d", g.bn);
-            return RGF_E_INVALID;
+    if (tc_bk() == 16) {
+        switch (g.bn) {
+            case 64: return launch_tc<kSlices, kGroups, 64, false, 16>(a, st);
+            case 80: return launch_tc<kSlices, kGroups, 80, false, 16>(a, st);
+            case 0:
+            case 96: return launch_tc<kSlices, kGroups, 96, false, 16>(a, st);
+            default: break;
+        }
+    } else {
+        switch (g.bn) {
+            case 64: return launch_tc<kSlices, kGroups, 64, false, 32>(a, st);
+            case 80: return launch_tc<kSlices, kGroups, 80, false, 32>(a, st);
+            case 0:
+            case 96: return launch_tc<kSlices, kGroups, 96, false, 32>(a, st);
+            default: break;
+        }
     }
+    set_error("oz_gemm_tc: unsupported tile width %d", g.bn);
+    return RGF_E_INVALID;
 }
 
 rgf_status oz_gemm_hp(const OzGemmHP& g, cudaStream_t st) {
     TcArgs a{g.batch, g.m, g.n, g.k, g.As, g.Bs, g.Kp, g.alpha, g.D, g.sD, g.add_identity, g.C, g.sC, g.active,
              g.status, TC_WAIT_NS, 0};
-    return launch_tc<kSlicesHP, kGroupsHP, 80, true>(a, st);
+    if (tc_bk() == 16) return launch_tc<kSlicesHP, kGroupsHP, 80, true, 16>(a, st);
+    return launch_tc<kSlicesHP, kGroupsHP, 80, true, 32>(a, st);
 }
 
 }  // namespace rgf
