@@ -345,6 +345,7 @@ def main():
     clocks = ClockSampler(local)
     rgf.rgf_gemm_timing(True)
     launches0 = rgf.rgf_launch_count()
+    phase0 = rgf.rgf_plan_phase_ms(plan.handle)
     barrier()
     torch.cuda.synchronize()
     clocks.start()
@@ -364,6 +365,7 @@ def main():
     barrier()
     clocks.stop()
     launches = rgf.rgf_launch_count() - launches0
+    phase1 = rgf.rgf_plan_phase_ms(plan.handle)
     gemm_ms, gemm_n, gemm_flops = rgf.rgf_gemm_timing(False)
     elapsed = ev0.elapsed_time(ev1) / 1e3
     per_step = [a.elapsed_time(b_) for a, b_ in step_ms]
@@ -466,6 +468,8 @@ def main():
         "parity_sample": {"energies": nb, "max_abs_dT": float(dT.max()), "bar": 1e-6},
         "fp64_gpu": fp64,
         "fp64_reseeds": reseeds,
+        "phases_ms_per_step": {"lead_decimation_sigma_gamma": (phase1[0] - phase0[0]) / args.steps,
+                               "layer_sweep_and_trace": (phase1[1] - phase0[1]) / args.steps},
         "flags_first_timed_wave": flag_counts,
         "clocks": clk,
     }

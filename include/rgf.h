@@ -150,6 +150,11 @@ rgf_status rgf_poll(rgf_ticket_t ticket, double* T, double* err, int* flags, int
  * run, and mixed-path inverses whose FP32 seed was replaced by an FP64 seed. */
 rgf_status rgf_plan_stats(rgf_plan_t plan, long long* waves, long long* fp64_reseeds);
 
+/* Device time (ms, CUDA events on the plan's stream) spent by the mixed path
+ * since the plan's creation in its two phases: lead decimation with the
+ * self-energies, and the layer sweep with the trace (0 for FP64 plans). */
+rgf_status rgf_plan_phase_ms(rgf_plan_t plan, double* lead_ms, double* sweep_ms);
+
 /* Device bytes the plan holds (blocks + workspace for one energy wave). */
 rgf_status rgf_plan_device_bytes(rgf_plan_t plan, size_t* bytes);
 

@@ -249,6 +249,13 @@ rgf_status rgf_plan_stats(rgf_plan_t p, long long* waves, long long* fp64_reseed
     return RGF_OK;
 }
 
+rgf_status rgf_plan_phase_ms(rgf_plan_t p, double* lead_ms, double* sweep_ms) {
+    RGF_TRY(check_plan(p));
+    if (lead_ms) *lead_ms = p->lead_ms;
+    if (sweep_ms) *sweep_ms = p->sweep_ms;
+    return RGF_OK;
+}
+
 rgf_status rgf_plan_energy_wave(rgf_plan_t p, int* w) {
     RGF_TRY(check_plan(p));
     if (!w) {

@@ -69,6 +69,11 @@ struct OzGemm {
     unsigned long long test_wait_ns;
     // Real output columns per CTA of the tcgen05 core: 64, 80 or 96 (0 = 96).
     int bn;
+    // Slices of each operand that take part: 6 (0 = 6, full double-float
+    // product) or 4 (ten pairs, relative error ~2^-30 of |A| |B|; enough for
+    // a Newton-Schulz correction X R, whose size is |X| |R| with R small and
+    // whose error the next residual, computed in full, measures again).
+    int nsl;
 };
 
 struct OzGemmHP {

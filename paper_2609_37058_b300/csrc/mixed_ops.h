@@ -87,6 +87,8 @@ rgf_status sliceA(const Ctx& c, int cnt, int ia, const float4* A, const int* act
 rgf_status sliceB(const Ctx& c, int cnt, int ib, const float4* B, const int* act);
 rgf_status mm(const Ctx& c, int cnt, int ia, int ib, float alpha, const float4* D, int addI, float4* C,
               const int* act);
+// C = A B + D from the four most significant slices of each operand.
+rgf_status mm4(const Ctx& c, int cnt, int ia, int ib, const float4* D, float4* C, const int* act);
 // Seven-slice (FP64-class) counterparts for FP64 matrices.
 rgf_status hsliceA(const Ctx& c, int cnt, int ia, const double2* A, const int* act);
 rgf_status hsliceB(const Ctx& c, int cnt, int ib, const double2* B, const int* act);
@@ -101,6 +103,7 @@ rgf_status inv_mixed(const Ctx& c, int cnt, int W, const float4* M, float4* X, f
 // The same for FP64 matrices with seven-slice products.
 rgf_status inv_hp(const Ctx& c, int cnt, int W, const double2* M, double2* X, double2* R, const int* act,
                   int* gj_flags);
+
 
 // Decimation pool unit u (u*W matrices in).  Units 0, 2, 4, 6 hold eps_s,
 // eps, alpha, beta of the 2W entries (s*W + e, s = side) on entry to

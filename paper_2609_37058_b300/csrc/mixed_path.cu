@@ -53,6 +53,26 @@ rgf_status mm(const Ctx& c, int cnt, int ia, int ib, float alpha, const float4* 
     return oz_gemm(g, c.m->core, c.st);
 }
 
+// C = A B + D with four of the six slices of each operand (corrections).
+rgf_status mm4(const Ctx& c, int cnt, int ia, int ib, const float4* D, float4* C, const int* act) {
+    OzGemm g{};
+    g.batch = cnt;
+    g.m = g.n = g.k = c.b;
+    g.As = c.m->sa[ia];
+    g.Bs = c.m->sb[ib];
+    g.Kp = c.m->Kp;
+    g.alpha = 1.0f;
+    g.D = D;
+    g.sD = c.nn;
+    g.C = C;
+    g.sC = c.nn;
+    g.active = act;
+    g.status = c.m->status;
+    g.bn = c.m->bn;
+    g.nsl = c.m->core == 1 ? 0 : 4;
+    return oz_gemm(g, c.m->core, c.st);
+}
+
 // Seven-slice (FP64-class) counterparts for FP64 matrices.
 rgf_status hsliceA(const Ctx& c, int cnt, int ia, const double2* A, const int* act) {
     return slice_rows_f64(cnt, c.b, c.b, A, c.nn, c.m->hsa[ia], c.m->Kp, act, c.st);
@@ -213,7 +233,7 @@ rgf_status inv_mixed(const Ctx& c, int cnt, int W, const float4* M, float4* X, f
         }
         RGF_TRY(sliceA(c, cnt, 0, X, cur));
         RGF_TRY(sliceB(c, cnt, 0, R, cur));
-        RGF_TRY(mm(c, cnt, 0, 0, 1.0f, X, 0, X, cur));  // X += X R
+        RGF_TRY(mm4(c, cnt, 0, 0, X, X, cur));  // X += X R (a correction: four slices suffice)
         std::swap(cur, nxt);
     }
     return RGF_OK;
@@ -480,7 +500,17 @@ rgf_status mixed_wave(rgf_plan_s* p, int W) {
     const double* E = p->d_E;
     Ctx c{m, st, nn, b, p->opt.ns_steps, p->d_err, p->d_flags, &p->n_reseeds};
     auto U = [&](int unit) { return m->pool + (long)unit * W * nn; };
+    cudaEvent_t ev[3];
+    for (auto& e : ev) RGF_CUDA_TRY(cudaEventCreate(&e));
+    struct EvGuard {
+        cudaEvent_t* e;
+        ~EvGuard() {
+            for (int i = 0; i < 3; ++i) cudaEventDestroy(e[i]);
+        }
+    } guard{ev};
+    RGF_CUDA_TRY(cudaEventRecord(ev[0], st));
     RGF_TRY(mixed_leads(p, W, c));
+    RGF_CUDA_TRY(cudaEventRecord(ev[1], st));
     float4* sigma = U(0);
     float4* gamma = U(2);
     float4* sigL = sigma;
@@ -538,6 +568,7 @@ rgf_status mixed_wave(rgf_plan_s* p, int W) {
     RGF_TRY(sliceB(c, W, 0, gamR, nullptr));
     RGF_TRY(mm(c, W, 0, 0, 1.0f, nullptr, 0, Yt, nullptr));
     RGF_TRY(trace_dfc(W, b, Xt, Yt, p->d_T, p->d_Ti, st));
+    RGF_CUDA_TRY(cudaEventRecord(ev[2], st));
 
     int h_status = 0;
     RGF_CUDA_TRY(cudaMemcpyAsync(&h_status, m->status, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -546,6 +577,11 @@ rgf_status mixed_wave(rgf_plan_s* p, int W) {
         set_error("tensor-core GEMM pipeline timed out (status 0x%x)", h_status);
         return RGF_E_CUDA;
     }
+    float t_lead = 0.f, t_sweep = 0.f;
+    RGF_CUDA_TRY(cudaEventElapsedTime(&t_lead, ev[0], ev[1]));
+    RGF_CUDA_TRY(cudaEventElapsedTime(&t_sweep, ev[1], ev[2]));
+    p->lead_ms += t_lead;
+    p->sweep_ms += t_sweep;
     return RGF_OK;
 }
 

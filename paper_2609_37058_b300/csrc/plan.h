@@ -46,6 +46,10 @@ struct rgf_plan_s {
     // Counters.
     long long n_waves = 0;
     long long n_reseeds = 0;
+    // Device time of the mixed path's phases (CUDA events on the plan's
+    // stream, accumulated over waves): lead decimation with Sigma/Gamma, and
+    // the layer sweep with the trace.
+    double lead_ms = 0.0, sweep_ms = 0.0;
 
     // Mixed-path state (allocated only for RGF_MIXED).
     void* mixed = nullptr;

@@ -11,8 +11,9 @@
 //     accumulating pair (i, j) in TMEM accumulator min(i + j, 4) (five
 //     accumulators x BN columns of the 512 allocated);
 //   * four warps read the accumulators back with tcgen05.ld and combine
-//     the groups into double-float results (TwoSum), apply the epilogue
-//     (sign, addend, identity) and store float4 (re_hi, re_lo, im_hi, im_lo).
+//     the groups with exact FP32 TwoSums into double-float results (or, for
+//     the FP64 variant, into an FP32 expansion rounded once to FP64), apply
+//     the epilogue (sign, addend, identity) and store.
 // Every wait on an mbarrier is bounded (2 s); a timeout sets a status bit
 // that the host turns into an error, and the CTA still releases its TMEM.
 #include <atomic>
@@ -139,15 +140,44 @@ __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// Groups 0..3 through exact TwoSums, the tail into the low word.
-__device__ __forceinline__ float2 combine5(float g0, float g1, float g2, float g3, float g4) {
-    const float2 s = two_sum(g0, g1);
-    const float2 t = two_sum(s.x, g2);
-    const float2 u = two_sum(t.x, g3);
-    float lo = s.y + t.y;
-    lo += u.y;
-    lo += g4;
-    return fast_two_sum(u.x, lo);
+// FP64 value of the sum of NGRP group values: a TwoSum cascade in FP32
+// leaves the rounded sum s and the exact errors e_1..e_{NGRP-1}; those are
+// summed again with TwoSum into t and a last correction f, and only
+// s + (t + f) is formed in FP64 (three conversions and two FP64 additions
+// per output instead of one of each per group: the FP64 pipe is narrow).
+template <int NGRP>
+__device__ __forceinline__ double sum_groups_f64(const float (&v)[NGRP][16], int idx) {
+    float s = v[0][idx];
+    float e[NGRP - 1];
+#pragma unroll
+    for (int gq = 1; gq < NGRP; ++gq) {
+        const float2 r = two_sum(s, v[gq][idx]);
+        s = r.x;
+        e[gq - 1] = r.y;
+    }
+    float t = e[0], f = 0.0f;
+#pragma unroll
+    for (int k = 1; k < NGRP - 1; ++k) {
+        const float2 r = two_sum(t, e[k]);
+        t = r.x;
+        f += r.y;
+    }
+    return (double)s + ((double)t + (double)f);
+}
+
+// Double-float value of the group sums: groups 0..NGRP-2 through exact
+// TwoSums, the last (tail) group into the low word.
+template <int NGRP>
+__device__ __forceinline__ float2 combine_df(const float (&v)[NGRP][16], int idx) {
+    float hi = v[0][idx], lo = 0.0f;
+#pragma unroll
+    for (int gq = 1; gq < NGRP - 1; ++gq) {
+        const float2 r = two_sum(hi, v[gq][idx]);
+        hi = r.x;
+        lo += r.y;
+    }
+    lo += v[NGRP - 1][idx];
+    return fast_two_sum(hi, lo);
 }
 }  // namespace
 
@@ -172,7 +202,7 @@ struct TcArgs {
     int skip_first_chunk;
 };
 
-template <int NSL, int NGRP, int BN, bool OUT64, int BK>
+template <int NSL, int NGRP, int BN, bool OUT64, int BK, int PL>
 __global__ void __launch_bounds__(128, 1)
     k_oz_tc(TcArgs g, const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB) {
     using Cfg = TcCfg<NSL, NGRP, BN, BK>;
@@ -218,8 +248,8 @@ __global__ void __launch_bounds__(128, 1)
             unsigned char* st = base + s * Cfg::STAGE;
 #pragma unroll
             for (int sl = 0; sl < NSL; ++sl) {
-                tma_load_3d(smem_u32(st + sl * Cfg::ATILE), &tmA, kc * BK, m0, bi * NSL + sl, fb);
-                tma_load_3d(smem_u32(st + NSL * Cfg::ATILE + sl * Cfg::BTILE), &tmB, kc * BK, n0, bi * NSL + sl,
+                tma_load_3d(smem_u32(st + sl * Cfg::ATILE), &tmA, kc * BK, m0, bi * PL + sl, fb);
+                tma_load_3d(smem_u32(st + NSL * Cfg::ATILE + sl * Cfg::BTILE), &tmB, kc * BK, n0, bi * PL + sl,
                             fb);
             }
         }
@@ -283,13 +313,8 @@ __global__ void __launch_bounds__(128, 1)
                     if (c >= g.n) continue;
                     const long o = (long)bi * g.sC + (long)r * g.n + c;
                     if constexpr (OUT64) {
-                        // Sum the groups in FP64, smallest first.
-                        double re = 0.0, im = 0.0;
-#pragma unroll
-                        for (int gq = NGRP - 1; gq >= 0; --gq) {
-                            re += (double)v[gq][2 * t];
-                            im += (double)v[gq][2 * t + 1];
-                        }
+                        double re = sum_groups_f64<NGRP>(v, 2 * t);
+                        double im = sum_groups_f64<NGRP>(v, 2 * t + 1);
                         if (g.alpha < 0.0f) {
                             re = -re;
                             im = -im;
@@ -302,9 +327,8 @@ __global__ void __launch_bounds__(128, 1)
                         if (g.add_identity && r == c) re += 1.0;
                         reinterpret_cast<double2*>(g.C)[o] = make_double2(re, im);
                     } else {
-                        float2 re = combine5(v[0][2 * t], v[1][2 * t], v[2][2 * t], v[3][2 * t], v[4][2 * t]);
-                        float2 im = combine5(v[0][2 * t + 1], v[1][2 * t + 1], v[2][2 * t + 1], v[3][2 * t + 1],
-                                             v[4][2 * t + 1]);
+                        float2 re = combine_df<NGRP>(v, 2 * t);
+                        float2 im = combine_df<NGRP>(v, 2 * t + 1);
                         if (g.alpha < 0.0f) {
                             re = df_neg(re);
                             im = df_neg(im);
@@ -373,7 +397,9 @@ static rgf_status encode_slices(CUtensorMap* map, const __nv_bfloat16* ptr, int 
     return RGF_OK;
 }
 
-template <int NSL, int NGRP, int BN, bool OUT64, int BK>
+// PL: slice planes per batch entry in the buffers (>= NSL; the kernel reads
+// the NSL most significant).
+template <int NSL, int NGRP, int BN, bool OUT64, int BK, int PL = NSL>
 static rgf_status launch_tc(const TcArgs& g, cudaStream_t st) {
     using Cfg = TcCfg<NSL, NGRP, BN, BK>;
     if (g.batch <= 0) return RGF_OK;
@@ -381,17 +407,17 @@ static rgf_status launch_tc(const TcArgs& g, cudaStream_t st) {
         set_error("oz_gemm_tc: bad slice layout");
         return RGF_E_INVALID;
     }
-    if (g.batch > 65535 || (long)g.batch * NSL > 0x7fffffffL) {
+    if (g.batch > 65535 || (long)g.batch * PL > 0x7fffffffL) {
         set_error("oz_gemm_tc: batch too large");
         return RGF_E_INVALID;
     }
     CUtensorMap ta, tb;
-    RGF_TRY(encode_slices(&ta, g.As, g.Kp, g.m, (long)g.batch * NSL, TC_BM, BK));
-    RGF_TRY(encode_slices(&tb, g.Bs, g.Kp, 2L * g.n, (long)g.batch * NSL, BN, BK));
+    RGF_TRY(encode_slices(&ta, g.As, g.Kp, g.m, (long)g.batch * PL, TC_BM, BK));
+    RGF_TRY(encode_slices(&tb, g.Bs, g.Kp, 2L * g.n, (long)g.batch * PL, BN, BK));
     static std::atomic<bool> attr{false};
     if (!attr.load()) {
         // Idempotent: threads that race here all set the same value.
-        RGF_CUDA_TRY(cudaFuncSetAttribute(k_oz_tc<NSL, NGRP, BN, OUT64, BK>,
+        RGF_CUDA_TRY(cudaFuncSetAttribute(k_oz_tc<NSL, NGRP, BN, OUT64, BK, PL>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM));
         attr.store(true);
     }
@@ -400,7 +426,7 @@ static rgf_status launch_tc(const TcArgs& g, cudaStream_t st) {
     const bool timed = gemm_timing_enabled() && g.active == nullptr;
     cudaEvent_t ev = nullptr;
     if (timed) gemm_timing_before(st, &ev);
-    k_oz_tc<NSL, NGRP, BN, OUT64, BK><<<grid, 128, Cfg::SMEM, st>>>(g, ta, tb);
+    k_oz_tc<NSL, NGRP, BN, OUT64, BK, PL><<<grid, 128, Cfg::SMEM, st>>>(g, ta, tb);
     RGF_LAUNCH_CHECK();
     if (timed) {
         // NSL(NSL+1)/2 slice-pair real products of M = m, N = 2n, K = 2k per batch entry.
@@ -427,7 +453,17 @@ rgf_status oz_gemm_tc(const OzGemm& g, cudaStream_t st) {
         a.wait_ns = g.test_wait_ns;
         a.skip_first_chunk = 1;
     }
-    if (tc_bk() == 16) {
+    if (g.nsl == 4) {
+        // Four of the six slices (ten pairs, four exact groups): for
+        // products whose result is a small correction (see OzGemm::nsl).
+        switch (g.bn) {
+            case 64: return launch_tc<4, 4, 64, false, 32, kSlices>(a, st);
+            case 80: return launch_tc<4, 4, 80, false, 32, kSlices>(a, st);
+            case 0:
+            case 96: return launch_tc<4, 4, 96, false, 32, kSlices>(a, st);
+            default: break;
+        }
+    } else if (tc_bk() == 16) {
         switch (g.bn) {
             case 64: return launch_tc<kSlices, kGroups, 64, false, 16>(a, st);
             case 80: return launch_tc<kSlices, kGroups, 80, false, 16>(a, st);

@@ -99,6 +99,7 @@ def lib():
         "rgf_inverse_f64_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, _P, _P]),
         "rgf_inverse_f64_noalloc_limit": (ctypes.c_size_t, []),
         "rgf_plan_stats": (ctypes.c_int, [_P] + [ctypes.POINTER(ctypes.c_longlong)] * 2),
+        "rgf_plan_phase_ms": (ctypes.c_int, [_P] + [ctypes.POINTER(ctypes.c_double)] * 2),
         "rgf_gemm_timing": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)]),
         "rgf_server_options_default": (None, [ctypes.POINTER(rgf_server_options)]),
@@ -232,6 +233,13 @@ def rgf_plan_stats(plan):
     w, r = ctypes.c_longlong(), ctypes.c_longlong()
     _check(lib().rgf_plan_stats(plan, ctypes.byref(w), ctypes.byref(r)), "rgf_plan_stats")
     return w.value, r.value
+
+
+def rgf_plan_phase_ms(plan):
+    """(lead_ms, sweep_ms) of the mixed path since the plan's creation."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(lib().rgf_plan_phase_ms(plan, ctypes.byref(a), ctypes.byref(b)), "rgf_plan_phase_ms")
+    return a.value, b.value
 
 
 def rgf_plan_destroy(plan):
