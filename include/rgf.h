@@ -86,8 +86,10 @@ typedef enum { RGF_LEAD_LEFT = 0, RGF_LEAD_RIGHT = 1 } rgf_side;
 #define RGF_FLAG_SINGULAR   0x4  /* an exactly zero pivot in an inverse     */
 #define RGF_FLAG_REFINE     0x8  /* mixed path: an FP32 inverse seed had
                                     ||I - M X||_F >= 0.5 and was replaced by
-                                    an FP64 seed, or the last Newton-Schulz
-                                    step left ||I - M X||_F above 3e-7      */
+                                    an FP64 seed (in the lead decimation
+                                    first by the previous iteration's
+                                    inverse), or the last Newton-Schulz step
+                                    left ||I - M X||_F above 3e-7           */
 
 typedef struct {
     int precision;     /* rgf_precision; default RGF_FP64 */

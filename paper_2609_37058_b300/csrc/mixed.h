@@ -52,6 +52,15 @@ rgf_status slice_rows(int batch, int m, int k, const float4* A, long sA, __nv_bf
 rgf_status slice_cols(int batch, int k, int n, const float4* B, long sB, __nv_bfloat16* out, int Kp,
                       int* colexp, const int* active, cudaStream_t st);
 
+// Slices of the coupling blocks formed on the fly for W energies (entry =
+// energy, z = E[e] + i eta; S, H one b x b df block each):
+//   form_slice_rows:     A-operand slices of tau  = z S - H;
+//   form_slice_cols_dag: B-operand slices of tau' = z S^dagger - H^dagger.
+rgf_status form_slice_rows(int W, int b, const double* E, double eta, const float4* S, const float4* H,
+                           __nv_bfloat16* out, int Kp, cudaStream_t st);
+rgf_status form_slice_cols_dag(int W, int b, const double* E, double eta, const float4* S, const float4* H,
+                               __nv_bfloat16* out, int Kp, cudaStream_t st);
+
 struct OzGemm {
     int batch, m, n, k;          // complex sizes: C (m x n) = A (m x k) B (k x n)
     const __nv_bfloat16* As;     // [batch][kSlices][m][Kp]
@@ -137,12 +146,15 @@ rgf_status axpy_dfc(int batch, int b, float alpha, const float4* X, float4* Y, c
 //     the residual is below |R_i|^2 <= 1e-13, so the entry is done);
 //   err[e] = max(err[e], estimated final residual); an entry still above
 //     3e-7 on the last step is flagged RGF_FLAG_REFINE.
+// more_count (may be null) counts the entries with next_act = 1.
 rgf_status ns_check(int batch, int W, int b, const float4* R, double* err, int* flags, int step, int max_steps,
-                    const int* act, int* next_act, int* bad, int* bad_count, double2* theta, cudaStream_t st);
+                    const int* act, int* next_act, int* bad, int* bad_count, double2* theta, cudaStream_t st,
+                    int* more_count = nullptr);
 // R[i] *= theta[i] (complex) where theta[i] != 1.
 rgf_status scale_theta(int batch, int b, float4* R, const double2* theta, const int* act, cudaStream_t st);
 rgf_status ns_check_f64(int batch, int W, int b, const double2* R, double* err, int* flags, int step, int max_steps,
-                        const int* act, int* next_act, int* bad, int* bad_count, cudaStream_t st);
+                        const int* act, int* next_act, int* bad, int* bad_count, cudaStream_t st,
+                        int* more_count = nullptr);
 rgf_status c128_to_c64(int batch, int b, const double2* X, float2* Y, const int* mask, cudaStream_t st);
 rgf_status c64_to_c128(int batch, int b, const float2* X, double2* Y, const int* mask, cudaStream_t st);
 // Masked conversions between df and FP64 complex (entries with mask[i]).
@@ -150,15 +162,12 @@ rgf_status dfc_to_c128(int batch, int b, const float4* X, double2* Y, const int*
 rgf_status c128_to_dfc(int batch, int b, const double2* X, float4* Y, const int* mask, cudaStream_t st);
 // out[i] = act ? act[i] : 1
 rgf_status mask_init(int batch, const int* act, int* out, cudaStream_t st);
+// For FP64 inverses reseeded from a nearby inverse (mask): still_bad where
+// |I - M X|_F >= 0.5 (counted), next_act = |R|_F > 3e-7 for the mask entries.
+rgf_status recheck_f64(int batch, int b, const double2* R, const int* mask, int* still_bad, int* count,
+                       int* next_act, cudaStream_t st);
 // *acc += *count (one thread)
 rgf_status accumulate_count(long long* acc, const int* count, cudaStream_t st);
-rgf_status ns_check_f64(int batch, int W, int b, const double2* R, double* err, int* flags, int step, int max_steps,
-                        const int* act, int* next_act, int* bad, int* bad_count, cudaStream_t st);
-rgf_status c128_to_c64(int batch, int b, const double2* X, float2* Y, const int* mask, cudaStream_t st);
-rgf_status c64_to_c128(int batch, int b, const float2* X, double2* Y, const int* mask, cudaStream_t st);
-// Masked conversions between df and FP64 complex (entries with mask[i]).
-rgf_status dfc_to_c128(int batch, int b, const float4* X, double2* Y, const int* mask, cudaStream_t st);
-rgf_status c128_to_dfc(int batch, int b, const double2* X, float4* Y, const int* mask, cudaStream_t st);
 // T[i] = Re sum X_jk conj(Y_jk) reduced in FP64 from df inputs.
 rgf_status trace_dfc(int batch, int b, const float4* X, const float4* Y, double* T, double* Ti, cudaStream_t st);
 

@@ -79,6 +79,108 @@ __global__ void __launch_bounds__(256) k_slice_rows(int m, int k, const float4* 
     }
 }
 
+// (zr + i zi) S' - H' in df for one element (S', H' already conjugated
+// when the caller needs the conjugate transpose).
+__device__ __forceinline__ float4 zsh_df(float2 zr, float2 zi, float4 sv, float4 hv) {
+    const float2 sr = re_of(sv), sim = im_of(sv);
+    const float2 re = df_sub(df_sub(df_mul(zr, sr), df_mul(zi, sim)), re_of(hv));
+    const float2 im = df_sub(df_add(df_mul(zr, sim), df_mul(zi, sr)), im_of(hv));
+    return cdf(re, im);
+}
+__device__ __forceinline__ float4 conj_df(float4 v) { return make_float4(v.x, v.y, -v.z, -v.w); }
+
+// A-operand slices of tau = z S - H (one warp per row, one batch entry per
+// energy; S, H shared b x b df blocks): the formed matrix never goes to
+// memory.  Same layout as k_slice_rows.
+__global__ void __launch_bounds__(256) k_form_slice_rows(int b, const double* __restrict__ E, double eta,
+                                                         const float4* __restrict__ S, const float4* __restrict__ H,
+                                                         __nv_bfloat16* __restrict__ out, int Kp) {
+    const int bi = blockIdx.y;
+    const int lane = threadIdx.x & 31;
+    const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (r >= b) return;
+    const float2 zr = df_from_double(E[bi]), zi = df_from_double(eta);
+    const float4* Sr = S + (long)r * b;
+    const float4* Hr = H + (long)r * b;
+    float mx = 0.0f;
+    for (int j = lane; j < b; j += 32) {
+        const float4 v = zsh_df(zr, zi, Sr[j], Hr[j]);
+        mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.z)));
+    }
+    mx = warp_max(mx);
+    const int e = exp_above(mx);
+    for (int j = lane; j < b; j += 32) {
+        const float4 v = zsh_df(zr, zi, Sr[j], Hr[j]);
+        float sr[kSlices], si[kSlices];
+        slice6(v.x, v.y, e, sr);
+        slice6(v.z, v.w, e, si);
+#pragma unroll
+        for (int s = 0; s < kSlices; ++s) {
+            __nv_bfloat162 p;
+            p.x = __float2bfloat16_rn(sr[s]);
+            p.y = __float2bfloat16_rn(si[s]);
+            *reinterpret_cast<__nv_bfloat162*>(out + (((long)bi * kSlices + s) * b + r) * Kp + 2 * j) = p;
+        }
+    }
+}
+
+// B-operand slices of tau' = z S^dagger - H^dagger (one warp per column c of
+// tau', i.e. per row c of S and H, read contiguously): same layout as
+// k_slice_cols, with no transposition pass.
+__global__ void __launch_bounds__(256) k_form_slice_cols_dag(int b, const double* __restrict__ E, double eta,
+                                                             const float4* __restrict__ S,
+                                                             const float4* __restrict__ H,
+                                                             __nv_bfloat16* __restrict__ out, int Kp) {
+    const int bi = blockIdx.y;
+    const int lane = threadIdx.x & 31;
+    const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (c >= b) return;
+    const float2 zr = df_from_double(E[bi]), zi = df_from_double(eta);
+    const float4* Sc = S + (long)c * b;
+    const float4* Hc = H + (long)c * b;
+    float mx = 0.0f;
+    for (int i = lane; i < b; i += 32) {
+        const float4 v = zsh_df(zr, zi, conj_df(Sc[i]), conj_df(Hc[i]));
+        mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.z)));
+    }
+    mx = warp_max(mx);
+    const int e = exp_above(mx);
+    const long rows = 2L * b;
+    for (int i = lane; i < b; i += 32) {
+        const float4 v = zsh_df(zr, zi, conj_df(Sc[i]), conj_df(Hc[i]));
+        float sr[kSlices], si[kSlices];
+        slice6(v.x, v.y, e, sr);
+        slice6(v.z, v.w, e, si);
+#pragma unroll
+        for (int s = 0; s < kSlices; ++s) {
+            __nv_bfloat16* base = out + (((long)bi * kSlices + s) * rows) * Kp;
+            __nv_bfloat162 p0, p1;
+            p0.x = __float2bfloat16_rn(sr[s]);
+            p0.y = __float2bfloat16_rn(-si[s]);
+            p1.x = __float2bfloat16_rn(si[s]);
+            p1.y = __float2bfloat16_rn(sr[s]);
+            *reinterpret_cast<__nv_bfloat162*>(base + (2L * c) * Kp + 2 * i) = p0;
+            *reinterpret_cast<__nv_bfloat162*>(base + (2L * c + 1) * Kp + 2 * i) = p1;
+        }
+    }
+}
+
+rgf_status form_slice_rows(int W, int b, const double* E, double eta, const float4* S, const float4* H,
+                           __nv_bfloat16* out, int Kp, cudaStream_t st) {
+    if (W <= 0) return RGF_OK;
+    k_form_slice_rows<<<dim3(ceil_div(b, 8), W), 256, 0, st>>>(b, E, eta, S, H, out, Kp);
+    RGF_LAUNCH_CHECK();
+    return RGF_OK;
+}
+
+rgf_status form_slice_cols_dag(int W, int b, const double* E, double eta, const float4* S, const float4* H,
+                               __nv_bfloat16* out, int Kp, cudaStream_t st) {
+    if (W <= 0) return RGF_OK;
+    k_form_slice_cols_dag<<<dim3(ceil_div(b, 8), W), 256, 0, st>>>(b, E, eta, S, H, out, Kp);
+    RGF_LAUNCH_CHECK();
+    return RGF_OK;
+}
+
 rgf_status slice_rows(int batch, int m, int k, const float4* A, long sA, __nv_bfloat16* out, int Kp,
                       const int* active, cudaStream_t st) {
     if (batch <= 0) return RGF_OK;
@@ -551,7 +653,8 @@ rgf_status axpy_dfc(int batch, int b, float alpha, const float4* X, float4* Y, c
 }
 
 __global__ void k_ns_check(int W, int b, const float4* R, double* err, int* flags, int step, int max_steps,
-                           const int* act, int* next_act, int* bad, int* bad_count, double2* theta) {
+                           const int* act, int* next_act, int* bad, int* bad_count, double2* theta,
+                           int* more_count) {
     const int bi = blockIdx.x;
     if (act && !act[bi]) {
         if (threadIdx.x == 0) {
@@ -608,6 +711,7 @@ __global__ void k_ns_check(int W, int b, const float4* R, double* err, int* flag
         }
         const bool more = !(t <= 3e-7);
         next_act[bi] = more ? 1 : 0;
+        if (more && more_count) atomicAdd(more_count, 1);
         if (more && step == max_steps - 1) atomicOr(flags + e, RGF_FLAG_REFINE);
         // Error estimate of the finished inverse: after this step's correction
         // the residual is about t^2; an entry that never got there reports
@@ -621,16 +725,18 @@ __global__ void k_ns_check(int W, int b, const float4* R, double* err, int* flag
 }
 
 rgf_status ns_check(int batch, int W, int b, const float4* R, double* err, int* flags, int step, int max_steps,
-                    const int* act, int* next_act, int* bad, int* bad_count, double2* theta, cudaStream_t st) {
+                    const int* act, int* next_act, int* bad, int* bad_count, double2* theta, cudaStream_t st,
+                    int* more_count) {
     if (batch <= 0) return RGF_OK;
-    k_ns_check<<<batch, 256, 0, st>>>(W, b, R, err, flags, step, max_steps, act, next_act, bad, bad_count, theta);
+    k_ns_check<<<batch, 256, 0, st>>>(W, b, R, err, flags, step, max_steps, act, next_act, bad, bad_count, theta,
+                                      more_count);
     RGF_LAUNCH_CHECK();
     return RGF_OK;
 }
 
 // Same bookkeeping as k_ns_check for an FP64 residual.
 __global__ void k_ns_check_f64(int W, int b, const double2* R, double* err, int* flags, int step, int max_steps,
-                               const int* act, int* next_act, int* bad, int* bad_count) {
+                               const int* act, int* next_act, int* bad, int* bad_count, int* more_count) {
     const int bi = blockIdx.x;
     if (act && !act[bi]) {
         if (threadIdx.x == 0) {
@@ -660,14 +766,16 @@ __global__ void k_ns_check_f64(int W, int b, const double2* R, double* err, int*
         }
         const bool more = !(t <= 3e-7);
         next_act[bi] = more ? 1 : 0;
+        if (more && more_count) atomicAdd(more_count, 1);
         if (more && step == max_steps - 1) atomicOr(flags + e, RGF_FLAG_REFINE);
     }
 }
 
 rgf_status ns_check_f64(int batch, int W, int b, const double2* R, double* err, int* flags, int step, int max_steps,
-                        const int* act, int* next_act, int* bad, int* bad_count, cudaStream_t st) {
+                        const int* act, int* next_act, int* bad, int* bad_count, cudaStream_t st, int* more_count) {
     if (batch <= 0) return RGF_OK;
-    k_ns_check_f64<<<batch, 256, 0, st>>>(W, b, R, err, flags, step, max_steps, act, next_act, bad, bad_count);
+    k_ns_check_f64<<<batch, 256, 0, st>>>(W, b, R, err, flags, step, max_steps, act, next_act, bad, bad_count,
+                                          more_count);
     RGF_LAUNCH_CHECK();
     return RGF_OK;
 }
@@ -762,6 +870,40 @@ __global__ void k_mask_init(int batch, const int* act, int* out) {
 rgf_status mask_init(int batch, const int* act, int* out, cudaStream_t st) {
     if (batch <= 0) return RGF_OK;
     k_mask_init<<<ceil_div(batch, 256), 256, 0, st>>>(batch, act, out);
+    RGF_LAUNCH_CHECK();
+    return RGF_OK;
+}
+
+// Second look at FP64 inverses whose seed was replaced by a nearby inverse:
+// for mask entries, still_bad = (|R|_F >= 0.5 or not finite), counted into
+// *count, and next_act = |R|_F > 3e-7 (or still bad); other entries keep
+// next_act and get still_bad = 0.
+__global__ void k_recheck_f64(int b, const double2* R, const int* mask, int* still_bad, int* count, int* next_act) {
+    const int bi = blockIdx.x;
+    if (!mask[bi]) {
+        if (threadIdx.x == 0) still_bad[bi] = 0;
+        return;
+    }
+    __shared__ double sh[32];
+    const long nn = (long)b * b, off = (long)bi * nn;
+    double s = 0.0;
+    for (long i = threadIdx.x; i < nn; i += blockDim.x) {
+        const double2 a = R[off + i];
+        s += a.x * a.x + a.y * a.y;
+    }
+    const double t = sqrt(block_sum_d(s, sh));
+    if (threadIdx.x == 0) {
+        const bool sb = !(isfinite(t) && t < 0.5);
+        still_bad[bi] = sb ? 1 : 0;
+        if (sb) atomicAdd(count, 1);
+        next_act[bi] = (sb || t > 3e-7) ? 1 : 0;
+    }
+}
+
+rgf_status recheck_f64(int batch, int b, const double2* R, const int* mask, int* still_bad, int* count,
+                       int* next_act, cudaStream_t st) {
+    if (batch <= 0) return RGF_OK;
+    k_recheck_f64<<<batch, 256, 0, st>>>(b, R, mask, still_bad, count, next_act);
     RGF_LAUNCH_CHECK();
     return RGF_OK;
 }

@@ -8,7 +8,7 @@
 namespace rgf {
 
 constexpr int kPoolUnits = 20;  // df matrices, in units of W
-constexpr int kDecUnits = 24;   // FP64 decimation matrices, in units of W
+constexpr int kDecUnits = 26;   // FP64 decimation matrices, in units of W
 
 // Workspace of W energies of block size b, with lead decimation for Wd
 // energies (2 Wd lead entries) at a time.
@@ -26,7 +26,10 @@ struct MixedState {
     long long* reseed_acc = nullptr;  // FP64 reseeds counted on the device (graph mode)
     int* nsact[2] = {};
     int* bad = nullptr;
+    int* bad2 = nullptr;     // entries still bad after a reseed from a nearby inverse
     int* bad_count = nullptr;
+    int* more_count = nullptr;  // entries that need another Newton-Schulz step
+    int* h_more = nullptr;      // pinned
     int* h_bad = nullptr;    // pinned
     double2* c128 = nullptr;
     void* inv64_ws = nullptr;
@@ -101,13 +104,16 @@ rgf_status hmm(const Ctx& c, int cnt, int ia, int ib, float alpha, const double2
 rgf_status inv_mixed(const Ctx& c, int cnt, int W, const float4* M, float4* X, float4* R, const int* act,
                      int* gj_flags);
 // The same for FP64 matrices with seven-slice products.
+// X_prev (optional): inverses of nearby matrices (the previous decimation
+// iteration's); entries whose FP32 seed does not contract try X_prev before
+// the FP64 Gauss-Jordan inverse.
 rgf_status inv_hp(const Ctx& c, int cnt, int W, const double2* M, double2* X, double2* R, const int* act,
-                  int* gj_flags);
+                  int* gj_flags, const double2* X_prev = nullptr);
 
 
 // Decimation pool unit u (u*W matrices in).  Units 0, 2, 4, 6 hold eps_s,
 // eps, alpha, beta of the 2W entries (s*W + e, s = side) on entry to
-// hp_decimate_run.
+// hp_decimate_run; units 8..25 are its scratch.
 inline double2* dec_unit(const MixedState* m, int W, int u) { return m->dec_pool + (long)u * W * m->b * m->b; }
 // Sancho-Rubio decimation of the 2W lead entries already formed in units
 // 0, 2, 4, 6 (FP64 storage, seven-slice products).  *g_out receives the 2W

@@ -103,7 +103,7 @@ rgf_status hmm(const Ctx& c, int cnt, int ia, int ib, float alpha, const double2
 // steps with seven-slice products (FP64-class), FP64 Gauss-Jordan reseed of
 // seeds that do not contract.  Uses hsa[1] for M, hsa[0]/hsb[0] for the steps.
 rgf_status inv_hp(const Ctx& c, int cnt, int W, const double2* M, double2* X, double2* R, const int* act,
-                  int* gj_flags) {
+                  int* gj_flags, const double2* X_prev) {
     MixedState* m = c.m;
     RGF_TRY(c128_to_c64(cnt, c.b, M, m->c64, act, c.st));
     RGF_TRY(inv_t<float2>(cnt, c.b, m->c64, c.nn, m->inv_ws, nullptr, act, c.st));
@@ -118,23 +118,43 @@ rgf_status inv_hp(const Ctx& c, int cnt, int W, const double2* M, double2* X, do
         RGF_TRY(hsliceB(c, cnt, 0, X, cur));
         RGF_TRY(hmm(c, cnt, 1, 0, -1.0f, nullptr, 1, R, cur));  // R = I - M X
         if (s == 0) RGF_CUDA_TRY(cudaMemsetAsync(m->bad_count, 0, sizeof(int), c.st));
-        RGF_TRY(ns_check_f64(cnt, W, c.b, R, c.err, c.flags, s, steps, cur, nxt, m->bad, m->bad_count, c.st));
+        RGF_CUDA_TRY(cudaMemsetAsync(m->more_count, 0, sizeof(int), c.st));
+        RGF_TRY(ns_check_f64(cnt, W, c.b, R, c.err, c.flags, s, steps, cur, nxt, m->bad, m->bad_count, c.st,
+                             m->more_count));
+        RGF_CUDA_TRY(cudaMemcpyAsync(m->h_more, m->more_count, sizeof(int), cudaMemcpyDeviceToHost, c.st));
+        if (s > 0) RGF_CUDA_TRY(cudaStreamSynchronize(c.st));
         if (s == 0) {
             RGF_CUDA_TRY(cudaMemcpyAsync(m->h_bad, m->bad_count, sizeof(int), cudaMemcpyDeviceToHost, c.st));
             RGF_CUDA_TRY(cudaStreamSynchronize(c.st));
-            if (*m->h_bad > 0) {
-                if (c.n_reseeds) *c.n_reseeds += *m->h_bad;
-                RGF_TRY(copy_f64(cnt, c.b, m->c128, M, m->bad, c.st));
-                RGF_TRY(inv_t<double2>(cnt, c.b, m->c128, c.nn, m->inv64_ws, gj_flags, m->bad, c.st));
-                RGF_TRY(copy_f64(cnt, c.b, X, m->c128, m->bad, c.st));
+            int n_bad = *m->h_bad;
+            int* need64 = m->bad;
+            if (n_bad > 0 && X_prev) {
+                // The nearby matrix's inverse as the seed of these entries.
+                RGF_TRY(copy_f64(cnt, c.b, X, X_prev, m->bad, c.st));
                 RGF_TRY(hsliceB(c, cnt, 0, X, m->bad));
                 RGF_TRY(hmm(c, cnt, 1, 0, -1.0f, nullptr, 1, R, m->bad));
+                RGF_CUDA_TRY(cudaMemsetAsync(m->bad_count, 0, sizeof(int), c.st));
+                RGF_TRY(recheck_f64(cnt, c.b, R, m->bad, m->bad2, m->bad_count, nxt, c.st));
+                RGF_CUDA_TRY(cudaMemcpyAsync(m->h_bad, m->bad_count, sizeof(int), cudaMemcpyDeviceToHost, c.st));
+                RGF_CUDA_TRY(cudaStreamSynchronize(c.st));
+                n_bad = *m->h_bad;
+                need64 = m->bad2;
+            }
+            if (n_bad > 0) {
+                if (c.n_reseeds) *c.n_reseeds += n_bad;
+                RGF_TRY(copy_f64(cnt, c.b, m->c128, M, need64, c.st));
+                RGF_TRY(inv_t<double2>(cnt, c.b, m->c128, c.nn, m->inv64_ws, gj_flags, need64, c.st));
+                RGF_TRY(copy_f64(cnt, c.b, X, m->c128, need64, c.st));
+                RGF_TRY(hsliceB(c, cnt, 0, X, need64));
+                RGF_TRY(hmm(c, cnt, 1, 0, -1.0f, nullptr, 1, R, need64));
             }
         }
         RGF_TRY(hsliceA(c, cnt, 0, X, cur));
         RGF_TRY(hsliceB(c, cnt, 0, R, cur));
         RGF_TRY(hmm(c, cnt, 0, 0, 1.0f, X, 0, X, cur));  // X += X R
         std::swap(cur, nxt);
+        // A zero count: every entry is done (reseeded entries always continue).
+        if (*m->h_more == 0) break;
     }
     return RGF_OK;
 }
@@ -147,7 +167,7 @@ rgf_status hp_decimate_run(const Ctx& c, int W, double tol, int max_iter, double
     const int b = c.b, W2 = 2 * W;
     auto U = [&](int unit) { return dec_unit(m, W, unit); };
     double2 *eps_s = U(0), *eps = U(2), *alpha = U(4), *beta = U(6), *g = U(8), *ga = U(10), *gb = U(12);
-    double2 *t1 = U(14), *t2 = U(16), *t3 = U(18), *t4 = U(20), *R = U(22);
+    double2 *t1 = U(14), *t2 = U(16), *t3 = U(18), *t4 = U(20), *R = U(22), *g_prev = U(24);
     RGF_TRY(fro_norm_f64(W2, b, eps, m->dec_anorm, st));
     std::vector<int> ones(W2, 1);
     RGF_CUDA_TRY(cudaMemcpyAsync(m->dec_active, ones.data(), sizeof(int) * W2, cudaMemcpyHostToDevice, st));
@@ -155,7 +175,12 @@ rgf_status hp_decimate_run(const Ctx& c, int W, double tol, int max_iter, double
     RGF_CUDA_TRY(cudaMemsetAsync(m->dec_flags, 0, sizeof(int) * W2, st));
     int* act = m->dec_active;
     for (int it = 1; it <= max_iter; ++it) {
-        RGF_TRY(inv_hp(c, W2, W, eps, g, R, act, m->dec_flags));
+        // From the second iteration on, entries whose FP32 seed does not
+        // contract start from the previous iteration's inverse (eps changes by
+        // alpha g beta + beta g alpha, which shrinks as the decimation
+        // converges) before resorting to an FP64 Gauss-Jordan inverse.
+        RGF_TRY(inv_hp(c, W2, W, eps, g, R, act, m->dec_flags, it > 1 ? g_prev : nullptr));
+        RGF_TRY(copy_f64(W2, b, g_prev, g, act, st));
         RGF_TRY(hsliceA(c, W2, 0, g, act));
         RGF_TRY(hsliceB(c, W2, 0, alpha, act));
         RGF_TRY(hmm(c, W2, 0, 0, 1.0f, nullptr, 0, ga, act));  // g alpha
@@ -210,7 +235,17 @@ rgf_status inv_mixed(const Ctx& c, int cnt, int W, const float4* M, float4* X, f
         RGF_TRY(sliceB(c, cnt, 0, X, cur));
         RGF_TRY(mm(c, cnt, 1, 0, -1.0f, nullptr, 1, R, cur));  // R = I - M X
         if (s == 1) RGF_CUDA_TRY(cudaMemsetAsync(m->bad_count, 0, sizeof(int), c.st));
-        RGF_TRY(ns_check(cnt, W, c.b, R, c.err, c.flags, s, steps, cur, nxt, m->bad, m->bad_count, m->theta, c.st));
+        // Outside graph capture, the number of entries that need a further
+        // step is read back from step 1 on (step 1 synchronises anyway), so
+        // that steps nobody needs are not launched.
+        const bool count_more = !c.graph && s >= 1;
+        if (count_more) RGF_CUDA_TRY(cudaMemsetAsync(m->more_count, 0, sizeof(int), c.st));
+        RGF_TRY(ns_check(cnt, W, c.b, R, c.err, c.flags, s, steps, cur, nxt, m->bad, m->bad_count, m->theta, c.st,
+                         count_more ? m->more_count : nullptr));
+        if (count_more && s >= 2) {
+            RGF_CUDA_TRY(cudaMemcpyAsync(m->h_more, m->more_count, sizeof(int), cudaMemcpyDeviceToHost, c.st));
+            RGF_CUDA_TRY(cudaStreamSynchronize(c.st));
+        }
         if (s == 0) RGF_TRY(scale_theta(cnt, c.b, R, m->theta, cur, c.st));
         if (s == 1 && c.graph) {
             RGF_TRY(accumulate_count(m->reseed_acc, m->bad_count, c.st));
@@ -221,6 +256,7 @@ rgf_status inv_mixed(const Ctx& c, int cnt, int W, const float4* M, float4* X, f
             RGF_TRY(mm(c, cnt, 1, 0, -1.0f, nullptr, 1, R, m->bad));
         } else if (s == 1) {
             RGF_CUDA_TRY(cudaMemcpyAsync(m->h_bad, m->bad_count, sizeof(int), cudaMemcpyDeviceToHost, c.st));
+            RGF_CUDA_TRY(cudaMemcpyAsync(m->h_more, m->more_count, sizeof(int), cudaMemcpyDeviceToHost, c.st));
             RGF_CUDA_TRY(cudaStreamSynchronize(c.st));
             if (*m->h_bad > 0) {
                 if (c.n_reseeds) *c.n_reseeds += *m->h_bad;
@@ -235,6 +271,9 @@ rgf_status inv_mixed(const Ctx& c, int cnt, int W, const float4* M, float4* X, f
         RGF_TRY(sliceB(c, cnt, 0, R, cur));
         RGF_TRY(mm4(c, cnt, 0, 0, X, X, cur));  // X += X R (a correction: four slices suffice)
         std::swap(cur, nxt);
+        // Entries reseeded in FP64 at step 1 always continue (their check saw
+        // the old seed), so a zero count means every entry is done.
+        if (count_more && *m->h_more == 0) break;
     }
     return RGF_OK;
 }
@@ -246,7 +285,7 @@ size_t mixed_workspace_bytes(int W, int b, int slice_entries, int inv_entries) {
     s += 2 * sa_bytes(slice_entries, b, Kp) + 2 * sb_bytes(slice_entries, b, Kp);
     s += (size_t)inv_entries * nn * sizeof(float2) + inv_workspace_bytes_t<float2>(inv_entries, b);
     s += (size_t)inv_entries * nn * sizeof(double2) + inv_workspace_bytes_t<double2>(inv_entries, b);
-    s += (size_t)inv_entries * b * sizeof(int) + (size_t)inv_entries * 3 * sizeof(int) +
+    s += (size_t)inv_entries * b * sizeof(int) + (size_t)inv_entries * 4 * sizeof(int) +
          (size_t)inv_entries * sizeof(double2) + 8192;
     return s;
 }
@@ -312,6 +351,8 @@ rgf_status mixed_state_init(MixedState* m, int b, int W, void* ws, cudaStream_t 
     w += (size_t)inv_entries * sizeof(int);
     m->bad = (int*)w;
     w += (size_t)inv_entries * sizeof(int);
+    m->bad2 = (int*)w;
+    w += (size_t)inv_entries * sizeof(int);
     w = (char*)(((uintptr_t)w + 15) & ~(uintptr_t)15);
     m->theta = (double2*)w;
     w += (size_t)inv_entries * sizeof(double2);
@@ -320,9 +361,10 @@ rgf_status mixed_state_init(MixedState* m, int b, int W, void* ws, cudaStream_t 
     // Zero the slice buffers once: the K padding is never written again.
     RGF_CUDA_TRY(cudaMemsetAsync(m->sa[0], 0,
                                  2 * sa_bytes(slice_entries, b, m->Kp) + 2 * sb_bytes(slice_entries, b, m->Kp), st));
-    RGF_TRY(alloc((void**)&m->status, 4 * sizeof(int)));
+    RGF_TRY(alloc((void**)&m->status, 8 * sizeof(int)));
     m->bad_count = m->status + 1;
     m->reseed_acc = (long long*)(m->status + 2);
+    m->more_count = m->status + 4;
     {
         char* d = nullptr;
         RGF_TRY(alloc((void**)&d, mixed_dec_bytes(Wd, b)));
@@ -351,13 +393,14 @@ rgf_status mixed_state_init(MixedState* m, int b, int W, void* ws, cudaStream_t 
                                      2 * sa_bytes(2 * Wd, b, m->Kp, kSlicesHP) + 2 * sb_bytes(2 * Wd, b, m->Kp, kSlicesHP),
                                      st));
     }
-    if (cudaMallocHost((void**)&m->h_bad, 2 * sizeof(int)) != cudaSuccess) {
+    if (cudaMallocHost((void**)&m->h_bad, 4 * sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         set_error("mixed workspace: cudaMallocHost failed");
         return RGF_E_OOM;
     }
     m->h_remaining = m->h_bad + 1;
-    RGF_CUDA_TRY(cudaMemsetAsync(m->status, 0, 4 * sizeof(int), st));
+    m->h_more = m->h_bad + 2;
+    RGF_CUDA_TRY(cudaMemsetAsync(m->status, 0, 8 * sizeof(int), st));
     RGF_CUDA_TRY(cudaStreamSynchronize(st));
     return RGF_OK;
 }
@@ -534,16 +577,13 @@ rgf_status mixed_wave(rgf_plan_s* p, int W) {
         for (int i = 1; i < N; ++i) {
             const float4* Sl = pm->S_lower + (long)(i - 1) * nn;
             const float4* Hl = pm->H_lower + (long)(i - 1) * nn;
-            FormSrcDf up{{Sl, nullptr}, {Hl, nullptr}, {1, 0}};
-            FormSrcDf lo{{Sl, nullptr}, {Hl, nullptr}, {0, 0}};
             FormSrcDf ai{{pm->S_diag + (long)i * nn, nullptr}, {pm->H_diag + (long)i * nn, nullptr}, {0, 0}};
-            RGF_TRY(form_dfc(W, 1, b, E, eta, up, Ut, nullptr, nullptr, st));
-            RGF_TRY(form_dfc(W, 1, b, E, eta, lo, Lt, nullptr, nullptr, st));
             RGF_TRY(form_dfc(W, 1, b, E, eta, ai, M, (i == N - 1) ? sigR : nullptr, nullptr, st));
+            // tau' and tau go straight to their slices (never stored as matrices).
             RGF_TRY(sliceA(c, W, 0, gi, nullptr));
-            RGF_TRY(sliceB(c, W, 0, Ut, nullptr));
+            RGF_TRY(form_slice_cols_dag(W, b, E, eta, Sl, Hl, m->sb[0], m->Kp, st));
             RGF_TRY(mm(c, W, 0, 0, -1.0f, nullptr, 0, P, nullptr));  // P = -g tau'
-            RGF_TRY(sliceA(c, W, 0, Lt, nullptr));
+            RGF_TRY(form_slice_rows(W, b, E, eta, Sl, Hl, m->sa[0], m->Kp, st));
             RGF_TRY(sliceB(c, W, 0, P, nullptr));
             RGF_TRY(mm(c, W, 0, 0, 1.0f, M, 0, M, nullptr));  // M += tau P
             if (i == 1) {
