@@ -24,7 +24,7 @@ struct SlotTab {
 // Masks that accompany a table of S slots (each an int[S] array).
 struct SlotMasks {
     const int* act;    // slot active this step
-    const int* nf;     // active and not on its first layer
+    const int* nf;     // active and not on its first layer (may be null)
     const int* first;  // active and on its first layer
     const int* last;   // active and on its last layer
     const int* refill; // slot starts a new item this step
@@ -50,9 +50,17 @@ rgf_status pad_f64(int nblk, int b, int bc, const double2* src, double2* dst, do
 rgf_status engine_refill(int S, int bc, const SlotTab* tab, const int* refill, const float4* ready,
                          float4* store, const double* dec_err, const int* dec_flags, double* slot_err,
                          int* slot_flags, cudaStream_t st);
+// BF16 slices of the slots' coupling blocks, formed on the fly from the
+// table (mask: slots past their first layer):
+//   form_slice_rows_tab:     A operand tau  = z S_{l,l-1} - H_{l,l-1};
+//   form_slice_cols_dag_tab: B operand tau' = z S_{l,l-1}^dagger - H_{l,l-1}^dagger.
+rgf_status form_slice_rows_tab(int S, int b, const SlotTab* tab, const int* mask, __nv_bfloat16* out, int Kp,
+                               cudaStream_t st);
+rgf_status form_slice_cols_dag_tab(int S, int b, const SlotTab* tab, const int* mask, __nv_bfloat16* out, int Kp,
+                                   cudaStream_t st);
 // M = z S_ll - H_ll - [first] Sigma_L - [last] Sigma_R for active slots;
 // Ut = z S_{l,l-1}^dagger - H_{l,l-1}^dagger, Lt = z S_{l,l-1} - H_{l,l-1}
-// for slots past their first layer.
+// for slots past their first layer (skipped when mk.nf is null).
 rgf_status engine_form_step(int S, int bc, const SlotTab* tab, SlotMasks mk, const float4* sigL, const float4* sigR,
                             float4* M, float4* Ut, float4* Lt, cudaStream_t st);
 rgf_status set_identity_masked_dfc(int S, int bc, float4* A, const int* mask, cudaStream_t st);

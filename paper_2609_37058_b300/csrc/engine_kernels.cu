@@ -89,7 +89,7 @@ __global__ void k_form_step(int S, int bc, const SlotTab* __restrict__ tab, Slot
     const int s = blockIdx.y;
     if (!mk.act[s]) return;
     const SlotTab t = tab[s];
-    const int nf = mk.nf[s], fi = mk.first[s], la = mk.last[s];
+    const int nf = mk.nf ? mk.nf[s] : 0, fi = mk.first[s], la = mk.last[s];
     const float2 zr = df_from_double(t.E), zi = df_from_double(t.eta);
     const long nn = (long)bc * bc, off = (long)s * nn;
     for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += (long)gridDim.x * blockDim.x) {

@@ -162,9 +162,8 @@ rgf_status slice_rows_f64(int batch, int m, int k, const double2* A, long sA, __
 }
 
 rgf_status slice_cols_f64(int batch, int k, int n, const double2* B, long sB, __nv_bfloat16* out, int Kp,
-                          int* colexp, const int* active, cudaStream_t st) {
+                          const int* active, cudaStream_t st) {
     if (batch <= 0) return RGF_OK;
-    (void)colexp;
     k_slice_cols_f64<<<dim3(ceil_div(n, 32), batch), 256, 0, st>>>(k, n, B, sB, out, Kp, active);
     RGF_LAUNCH_CHECK();
     return RGF_OK;

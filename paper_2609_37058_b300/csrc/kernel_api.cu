@@ -138,7 +138,7 @@ static rgf_status zgemm_mixed_impl(int batch, int m, int n, int k, const double*
     if (batch == 0) return RGF_OK;
     const size_t sa = (size_t)m * k, sb = (size_t)k * n, sc = (size_t)m * n;
     const int Kp = rgf::slice_pitch(k);
-    DevBuf dA, dB, fA, fB, fC, dC, SA, SB, cexp, status;
+    DevBuf dA, dB, fA, fB, fC, dC, SA, SB, status;
     RGF_TRY(dalloc(dA, batch * sa * 16));
     RGF_TRY(dalloc(dB, batch * sb * 16));
     RGF_TRY(dalloc(fA, batch * sa * 16));
@@ -148,7 +148,6 @@ static rgf_status zgemm_mixed_impl(int batch, int m, int n, int k, const double*
     const size_t sab = (size_t)batch * rgf::kSlices * m * Kp * 2, sbb = (size_t)batch * rgf::kSlices * 2 * n * Kp * 2;
     RGF_TRY(dalloc(SA, sab));
     RGF_TRY(dalloc(SB, sbb));
-    RGF_TRY(dalloc(cexp, (size_t)batch * n * sizeof(int)));
     RGF_TRY(dalloc(status, sizeof(int)));
     RGF_CUDA_TRY(cudaMemset(SA.p, 0, sab));
     RGF_CUDA_TRY(cudaMemset(SB.p, 0, sbb));
@@ -158,7 +157,7 @@ static rgf_status zgemm_mixed_impl(int batch, int m, int n, int k, const double*
     RGF_TRY(rgf::to_dfc((long)(batch * sa), (const double2*)dA.p, (float4*)fA.p, 0));
     RGF_TRY(rgf::to_dfc((long)(batch * sb), (const double2*)dB.p, (float4*)fB.p, 0));
     RGF_TRY(rgf::slice_rows(batch, m, k, (const float4*)fA.p, (long)sa, (__nv_bfloat16*)SA.p, Kp, nullptr, 0));
-    RGF_TRY(rgf::slice_cols(batch, k, n, (const float4*)fB.p, (long)sb, (__nv_bfloat16*)SB.p, Kp, (int*)cexp.p,
+    RGF_TRY(rgf::slice_cols(batch, k, n, (const float4*)fB.p, (long)sb, (__nv_bfloat16*)SB.p, Kp,
                             nullptr, 0));
     rgf::OzGemm g{};
     g.batch = batch;
@@ -195,14 +194,13 @@ rgf_status rgf_kernel_zgemm_hp(int batch, int m, int n, int k, const double* A, 
     if (batch == 0) return RGF_OK;
     const size_t sa = (size_t)m * k, sb = (size_t)k * n, sc = (size_t)m * n;
     const int Kp = rgf::slice_pitch(k);
-    DevBuf dA, dB, dC, SA, SB, cexp, status;
+    DevBuf dA, dB, dC, SA, SB, status;
     RGF_TRY(dalloc(dA, batch * sa * 16));
     RGF_TRY(dalloc(dB, batch * sb * 16));
     RGF_TRY(dalloc(dC, batch * sc * 16));
     const size_t sab = (size_t)batch * rgf::kSlicesHP * m * Kp * 2, sbb = (size_t)batch * rgf::kSlicesHP * 2 * n * Kp * 2;
     RGF_TRY(dalloc(SA, sab));
     RGF_TRY(dalloc(SB, sbb));
-    RGF_TRY(dalloc(cexp, (size_t)batch * n * sizeof(int)));
     RGF_TRY(dalloc(status, sizeof(int)));
     RGF_CUDA_TRY(cudaMemset(SA.p, 0, sab));
     RGF_CUDA_TRY(cudaMemset(SB.p, 0, sbb));
@@ -210,7 +208,7 @@ rgf_status rgf_kernel_zgemm_hp(int batch, int m, int n, int k, const double* A, 
     RGF_CUDA_TRY(cudaMemcpy(dA.p, A, batch * sa * 16, cudaMemcpyHostToDevice));
     RGF_CUDA_TRY(cudaMemcpy(dB.p, B, batch * sb * 16, cudaMemcpyHostToDevice));
     RGF_TRY(rgf::slice_rows_f64(batch, m, k, (const double2*)dA.p, (long)sa, (__nv_bfloat16*)SA.p, Kp, nullptr, 0));
-    RGF_TRY(rgf::slice_cols_f64(batch, k, n, (const double2*)dB.p, (long)sb, (__nv_bfloat16*)SB.p, Kp, (int*)cexp.p,
+    RGF_TRY(rgf::slice_cols_f64(batch, k, n, (const double2*)dB.p, (long)sb, (__nv_bfloat16*)SB.p, Kp,
                                 nullptr, 0));
     rgf::OzGemmHP g{};
     g.batch = batch;

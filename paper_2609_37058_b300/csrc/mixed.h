@@ -48,9 +48,8 @@ rgf_status slice_rows(int batch, int m, int k, const float4* A, long sA, __nv_bf
 //   row 2c  : (Re B[j][c], -Im B[j][c]) at K positions (2j, 2j+1)
 //   row 2c+1: (Im B[j][c],  Re B[j][c])
 // so that one real GEMM gives Re C in real column 2c and Im C in 2c+1.
-// colexp is int scratch of batch*n entries.
 rgf_status slice_cols(int batch, int k, int n, const float4* B, long sB, __nv_bfloat16* out, int Kp,
-                      int* colexp, const int* active, cudaStream_t st);
+                      const int* active, cudaStream_t st);
 
 // Slices of the coupling blocks formed on the fly for W energies (entry =
 // energy, z = E[e] + i eta; S, H one b x b df block each):
@@ -104,7 +103,7 @@ rgf_status oz_gemm_hp(const OzGemmHP& g, cudaStream_t st);
 rgf_status slice_rows_f64(int batch, int m, int k, const double2* A, long sA, __nv_bfloat16* out, int Kp,
                           const int* active, cudaStream_t st);
 rgf_status slice_cols_f64(int batch, int k, int n, const double2* B, long sB, __nv_bfloat16* out, int Kp,
-                          int* colexp, const int* active, cudaStream_t st);
+                          const int* active, cudaStream_t st);
 
 // Reference core on the legacy warp-level tensor path (mma.sync BF16).
 rgf_status oz_gemm_mma(const OzGemm& g, cudaStream_t st);

@@ -4,6 +4,7 @@
 // broadenings, Newton-Schulz bookkeeping, the FP64 trace reduction).
 #include <atomic>
 #include "df.cuh"
+#include "engine.h"
 #include "mixed.h"
 
 namespace rgf {
@@ -165,6 +166,98 @@ __global__ void __launch_bounds__(256) k_form_slice_cols_dag(int b, const double
     }
 }
 
+// Table-driven forms of the two kernels above for the server's energy
+// slots: entry s reads its own coupling blocks tab[s].Sl, tab[s].Hl and
+// energy tab[s].E + i tab[s].eta, and is skipped unless mask[s].
+__global__ void __launch_bounds__(256) k_form_slice_rows_tab(int b, const SlotTab* __restrict__ tab,
+                                                             const int* __restrict__ mask,
+                                                             __nv_bfloat16* __restrict__ out, int Kp) {
+    const int bi = blockIdx.y;
+    if (!mask[bi]) return;
+    const int lane = threadIdx.x & 31;
+    const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (r >= b) return;
+    const SlotTab t = tab[bi];
+    const float2 zr = df_from_double(t.E), zi = df_from_double(t.eta);
+    const float4* Sr = t.Sl + (long)r * b;
+    const float4* Hr = t.Hl + (long)r * b;
+    float mx = 0.0f;
+    for (int j = lane; j < b; j += 32) {
+        const float4 v = zsh_df(zr, zi, Sr[j], Hr[j]);
+        mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.z)));
+    }
+    mx = warp_max(mx);
+    const int e = exp_above(mx);
+    for (int j = lane; j < b; j += 32) {
+        const float4 v = zsh_df(zr, zi, Sr[j], Hr[j]);
+        float sr[kSlices], si[kSlices];
+        slice6(v.x, v.y, e, sr);
+        slice6(v.z, v.w, e, si);
+#pragma unroll
+        for (int s = 0; s < kSlices; ++s) {
+            __nv_bfloat162 p;
+            p.x = __float2bfloat16_rn(sr[s]);
+            p.y = __float2bfloat16_rn(si[s]);
+            *reinterpret_cast<__nv_bfloat162*>(out + (((long)bi * kSlices + s) * b + r) * Kp + 2 * j) = p;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_form_slice_cols_dag_tab(int b, const SlotTab* __restrict__ tab,
+                                                                 const int* __restrict__ mask,
+                                                                 __nv_bfloat16* __restrict__ out, int Kp) {
+    const int bi = blockIdx.y;
+    if (!mask[bi]) return;
+    const int lane = threadIdx.x & 31;
+    const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (c >= b) return;
+    const SlotTab t = tab[bi];
+    const float2 zr = df_from_double(t.E), zi = df_from_double(t.eta);
+    const float4* Sc = t.Sl + (long)c * b;
+    const float4* Hc = t.Hl + (long)c * b;
+    float mx = 0.0f;
+    for (int i = lane; i < b; i += 32) {
+        const float4 v = zsh_df(zr, zi, conj_df(Sc[i]), conj_df(Hc[i]));
+        mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.z)));
+    }
+    mx = warp_max(mx);
+    const int e = exp_above(mx);
+    const long rows = 2L * b;
+    for (int i = lane; i < b; i += 32) {
+        const float4 v = zsh_df(zr, zi, conj_df(Sc[i]), conj_df(Hc[i]));
+        float sr[kSlices], si[kSlices];
+        slice6(v.x, v.y, e, sr);
+        slice6(v.z, v.w, e, si);
+#pragma unroll
+        for (int s = 0; s < kSlices; ++s) {
+            __nv_bfloat16* base = out + (((long)bi * kSlices + s) * rows) * Kp;
+            __nv_bfloat162 p0, p1;
+            p0.x = __float2bfloat16_rn(sr[s]);
+            p0.y = __float2bfloat16_rn(-si[s]);
+            p1.x = __float2bfloat16_rn(si[s]);
+            p1.y = __float2bfloat16_rn(sr[s]);
+            *reinterpret_cast<__nv_bfloat162*>(base + (2L * c) * Kp + 2 * i) = p0;
+            *reinterpret_cast<__nv_bfloat162*>(base + (2L * c + 1) * Kp + 2 * i) = p1;
+        }
+    }
+}
+
+rgf_status form_slice_rows_tab(int S, int b, const SlotTab* tab, const int* mask, __nv_bfloat16* out, int Kp,
+                               cudaStream_t st) {
+    if (S <= 0) return RGF_OK;
+    k_form_slice_rows_tab<<<dim3(ceil_div(b, 8), S), 256, 0, st>>>(b, tab, mask, out, Kp);
+    RGF_LAUNCH_CHECK();
+    return RGF_OK;
+}
+
+rgf_status form_slice_cols_dag_tab(int S, int b, const SlotTab* tab, const int* mask, __nv_bfloat16* out, int Kp,
+                                   cudaStream_t st) {
+    if (S <= 0) return RGF_OK;
+    k_form_slice_cols_dag_tab<<<dim3(ceil_div(b, 8), S), 256, 0, st>>>(b, tab, mask, out, Kp);
+    RGF_LAUNCH_CHECK();
+    return RGF_OK;
+}
+
 rgf_status form_slice_rows(int W, int b, const double* E, double eta, const float4* S, const float4* H,
                            __nv_bfloat16* out, int Kp, cudaStream_t st) {
     if (W <= 0) return RGF_OK;
@@ -253,10 +346,9 @@ __global__ void __launch_bounds__(256) k_slice_cols(int k, int n, const float4* 
     }
 }
 
-rgf_status slice_cols(int batch, int k, int n, const float4* B, long sB, __nv_bfloat16* out, int Kp, int* colexp,
+rgf_status slice_cols(int batch, int k, int n, const float4* B, long sB, __nv_bfloat16* out, int Kp,
                       const int* active, cudaStream_t st) {
     if (batch <= 0) return RGF_OK;
-    (void)colexp;
     k_slice_cols<<<dim3(ceil_div(n, 32), batch), 256, 0, st>>>(k, n, B, sB, out, Kp, active);
     RGF_LAUNCH_CHECK();
     return RGF_OK;

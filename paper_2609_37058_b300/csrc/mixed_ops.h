@@ -19,7 +19,6 @@ struct MixedState {
     float4* pool = nullptr;  // kPoolUnits * W df matrices
     __nv_bfloat16* sa[2] = {};
     __nv_bfloat16* sb[2] = {};
-    int* colexp = nullptr;
     float2* c64 = nullptr;
     void* inv_ws = nullptr;
     int* status = nullptr;   // tcgen05 pipeline timeout word
@@ -103,6 +102,11 @@ rgf_status hmm(const Ctx& c, int cnt, int ia, int ib, float alpha, const double2
 // contract.  R is df scratch of cnt matrices.
 rgf_status inv_mixed(const Ctx& c, int cnt, int W, const float4* M, float4* X, float4* R, const int* act,
                      int* gj_flags);
+// The same in parts: the seed (when s_begin == 0) and Newton-Schulz steps
+// s_begin .. s_end-1.  From step 1 on, MixedState::more_count holds the
+// number of entries that need another step.
+rgf_status inv_mixed_steps(const Ctx& c, int cnt, int W, const float4* M, float4* X, float4* R, const int* act,
+                           int* gj_flags, int s_begin, int s_end);
 // The same for FP64 matrices with seven-slice products.
 // X_prev (optional): inverses of nearby matrices (the previous decimation
 // iteration's); entries whose FP32 seed does not contract try X_prev before

@@ -30,7 +30,7 @@ rgf_status sliceA(const Ctx& c, int cnt, int ia, const float4* A, const int* act
     return slice_rows(cnt, c.b, c.b, A, c.nn, c.m->sa[ia], c.m->Kp, act, c.st);
 }
 rgf_status sliceB(const Ctx& c, int cnt, int ib, const float4* B, const int* act) {
-    return slice_cols(cnt, c.b, c.b, B, c.nn, c.m->sb[ib], c.m->Kp, c.m->colexp, act, c.st);
+    return slice_cols(cnt, c.b, c.b, B, c.nn, c.m->sb[ib], c.m->Kp, act, c.st);
 }
 // C = alpha * A B (+ D) (+ I) from already sliced operands.
 rgf_status mm(const Ctx& c, int cnt, int ia, int ib, float alpha, const float4* D, int addI, float4* C,
@@ -78,7 +78,7 @@ rgf_status hsliceA(const Ctx& c, int cnt, int ia, const double2* A, const int* a
     return slice_rows_f64(cnt, c.b, c.b, A, c.nn, c.m->hsa[ia], c.m->Kp, act, c.st);
 }
 rgf_status hsliceB(const Ctx& c, int cnt, int ib, const double2* B, const int* act) {
-    return slice_cols_f64(cnt, c.b, c.b, B, c.nn, c.m->hsb[ib], c.m->Kp, c.m->colexp, act, c.st);
+    return slice_cols_f64(cnt, c.b, c.b, B, c.nn, c.m->hsb[ib], c.m->Kp, act, c.st);
 }
 rgf_status hmm(const Ctx& c, int cnt, int ia, int ib, float alpha, const double2* D, int addI, double2* C,
                const int* act) {
@@ -219,30 +219,40 @@ rgf_status hp_decimate_run(const Ctx& c, int W, double tol, int max_iter, double
 // Uses sa[1] for M, sa[0]/sb[0] for the steps and R as df scratch.
 rgf_status inv_mixed(const Ctx& c, int cnt, int W, const float4* M, float4* X, float4* R, const int* act,
                      int* gj_flags) {
+    return inv_mixed_steps(c, cnt, W, M, X, R, act, gj_flags, 0, c.ns_steps);
+}
+
+rgf_status inv_mixed_steps(const Ctx& c, int cnt, int W, const float4* M, float4* X, float4* R, const int* act,
+                           int* gj_flags, int s_begin, int s_end) {
     MixedState* m = c.m;
-    RGF_TRY(dfc_hi_to_c64(cnt, c.b, M, m->c64, act, c.st));
-    // An FP32 seed with a zero pivot is not reported: its residual is not
-    // finite, so it is reseeded in FP64 below, which reports its own pivots.
-    RGF_TRY(inv_t<float2>(cnt, c.b, m->c64, c.nn, m->inv_ws, nullptr, act, c.st, m->gj_nb));
-    RGF_TRY(c64_to_dfc(cnt, c.b, m->c64, X, act, c.st));
     const int steps = c.ns_steps;
-    if (steps == 0) return RGF_OK;
-    int* cur = m->nsact[0];
-    int* nxt = m->nsact[1];
-    RGF_TRY(mask_init(cnt, act, cur, c.st));
-    RGF_TRY(sliceA(c, cnt, 1, M, act));
-    for (int s = 0; s < steps; ++s) {
+    if (s_end > steps) s_end = steps;
+    if (s_begin == 0) {
+        RGF_TRY(dfc_hi_to_c64(cnt, c.b, M, m->c64, act, c.st));
+        // An FP32 seed with a zero pivot is not reported: its residual is not
+        // finite, so it is reseeded in FP64 below, which reports its own pivots.
+        RGF_TRY(inv_t<float2>(cnt, c.b, m->c64, c.nn, m->inv_ws, nullptr, act, c.st, m->gj_nb));
+        RGF_TRY(c64_to_dfc(cnt, c.b, m->c64, X, act, c.st));
+        if (steps == 0) return RGF_OK;
+        RGF_TRY(mask_init(cnt, act, m->nsact[0], c.st));
+        RGF_TRY(sliceA(c, cnt, 1, M, act));
+    }
+    // Step s works on the mask nsact[s % 2] and writes nsact[(s + 1) % 2].
+    int* cur = m->nsact[s_begin & 1];
+    int* nxt = m->nsact[(s_begin + 1) & 1];
+    for (int s = s_begin; s < s_end; ++s) {
         RGF_TRY(sliceB(c, cnt, 0, X, cur));
         RGF_TRY(mm(c, cnt, 1, 0, -1.0f, nullptr, 1, R, cur));  // R = I - M X
         if (s == 1) RGF_CUDA_TRY(cudaMemsetAsync(m->bad_count, 0, sizeof(int), c.st));
-        // Outside graph capture, the number of entries that need a further
-        // step is read back from step 1 on (step 1 synchronises anyway), so
-        // that steps nobody needs are not launched.
-        const bool count_more = !c.graph && s >= 1;
+        // From step 1 on the entries that need a further step are counted.
+        // Outside graph capture the count is read back (step 1 synchronises
+        // anyway) so that steps nobody needs are not launched; in a graph the
+        // caller reads it after the step-1 graph.
+        const bool count_more = s >= 1;
         if (count_more) RGF_CUDA_TRY(cudaMemsetAsync(m->more_count, 0, sizeof(int), c.st));
         RGF_TRY(ns_check(cnt, W, c.b, R, c.err, c.flags, s, steps, cur, nxt, m->bad, m->bad_count, m->theta, c.st,
                          count_more ? m->more_count : nullptr));
-        if (count_more && s >= 2) {
+        if (count_more && !c.graph && s >= 2) {
             RGF_CUDA_TRY(cudaMemcpyAsync(m->h_more, m->more_count, sizeof(int), cudaMemcpyDeviceToHost, c.st));
             RGF_CUDA_TRY(cudaStreamSynchronize(c.st));
         }
@@ -273,7 +283,7 @@ rgf_status inv_mixed(const Ctx& c, int cnt, int W, const float4* M, float4* X, f
         std::swap(cur, nxt);
         // Entries reseeded in FP64 at step 1 always continue (their check saw
         // the old seed), so a zero count means every entry is done.
-        if (count_more && *m->h_more == 0) break;
+        if (count_more && !c.graph && *m->h_more == 0) break;
     }
     return RGF_OK;
 }
@@ -285,7 +295,7 @@ size_t mixed_workspace_bytes(int W, int b, int slice_entries, int inv_entries) {
     s += 2 * sa_bytes(slice_entries, b, Kp) + 2 * sb_bytes(slice_entries, b, Kp);
     s += (size_t)inv_entries * nn * sizeof(float2) + inv_workspace_bytes_t<float2>(inv_entries, b);
     s += (size_t)inv_entries * nn * sizeof(double2) + inv_workspace_bytes_t<double2>(inv_entries, b);
-    s += (size_t)inv_entries * b * sizeof(int) + (size_t)inv_entries * 4 * sizeof(int) +
+    s += (size_t)inv_entries * 4 * sizeof(int) +
          (size_t)inv_entries * sizeof(double2) + 8192;
     return s;
 }
@@ -357,7 +367,6 @@ rgf_status mixed_state_init(MixedState* m, int b, int W, void* ws, cudaStream_t 
     m->theta = (double2*)w;
     w += (size_t)inv_entries * sizeof(double2);
     w = (char*)(((uintptr_t)w + 255) & ~(uintptr_t)255);
-    m->colexp = (int*)w;
     // Zero the slice buffers once: the K padding is never written again.
     RGF_CUDA_TRY(cudaMemsetAsync(m->sa[0], 0,
                                  2 * sa_bytes(slice_entries, b, m->Kp) + 2 * sb_bytes(slice_entries, b, m->Kp), st));
@@ -562,7 +571,7 @@ rgf_status mixed_wave(rgf_plan_s* p, int W) {
     float4* gamR = gamma + (long)W * nn;
 
     // ---------------------------------------------------------- sweep
-    float4 *gi = U(4), *P = U(5), *M = U(6), *Lt = U(7), *Ut = U(8), *Q = U(9), *Qn = U(10);
+    float4 *gi = U(4), *P = U(5), *M = U(6), *Q = U(9), *Qn = U(10);
     float4 *G = U(11), *Xt = U(12), *Yt = U(13), *Rs = U(14);
     if (N == 1) {
         FormSrcDf a0{{pm->S_diag, nullptr}, {pm->H_diag, nullptr}, {0, 0}};

@@ -85,7 +85,9 @@ struct Engine {
     int* h_masks = nullptr;    // pinned
     DecTab* h_dtab = nullptr;  // pinned
     bool graphs = true;             // replay each step as a CUDA graph
-    cudaGraphExec_t gx[2] = {};     // one per Q/Qn parity
+    cudaGraphExec_t gx[2] = {};      // step front, one per Q/Qn parity
+    cudaGraphExec_t gx_back[2] = {}; // step back (G, trace, results), per parity
+    cudaGraphExec_t gx_tail = nullptr;  // Newton-Schulz steps beyond the second
     int parity = 0;                 // 0: Q = unit 9, 1: Q = unit 10
     std::atomic<long long> steps{0}, decs{0};
     long long reseeds = 0;  // engine thread; copied to reseeds_seen after each step
@@ -182,6 +184,9 @@ void engine_free(Engine* e) {
     if (e->h_dtab) cudaFreeHost(e->h_dtab);
     for (auto& g : e->gx)
         if (g) cudaGraphExecDestroy(g);
+    for (auto& g : e->gx_back)
+        if (g) cudaGraphExecDestroy(g);
+    if (e->gx_tail) cudaGraphExecDestroy(e->gx_tail);
     mixed_state_free(&e->ms);
     if (e->st) cudaStreamDestroy(e->st);
 }
@@ -250,12 +255,22 @@ rgf_status engine_decimate(Engine* e, const std::vector<std::pair<Request*, int>
     return RGF_OK;
 }
 
-// Kernels of one layer for every active slot.  With all = true every kernel
-// is launched (masks select the entries) so that the sequence is the same
-// every step and can be captured as a graph; Q/Qn are the buffers of the
-// given parity.
-rgf_status engine_issue(Engine* e, bool all, int n_nf, int n_first, int n_last, int n_refill, float4* Q,
-                        float4* Qn) {
+// Kernels of one layer for every active slot, in three parts so that the
+// Newton-Schulz steps beyond the second (rarely needed) can be skipped:
+//   front: table copy, refills, block formation, the P / M / Q products,
+//          the inverse's seed and Newton-Schulz steps 0 and 1 (with the FP64
+//          reseed of entries that do not contract), and the read-back of how
+//          many entries need a further step;
+//   tail:  Newton-Schulz steps 2 .. ns_steps-1;
+//   back:  G = Q g, the trace and the results of slots on their last layer.
+// With all = true every kernel is launched (masks select the entries), so
+// that each part is the same sequence every step and can be captured as a
+// graph; Q/Qn are the buffers of the step's parity.
+struct StepCounts {
+    int n_nf = 0, n_first = 0, n_last = 0, n_refill = 0;
+};
+
+rgf_status engine_front(Engine* e, bool all, const StepCounts& n, float4* Q, float4* Qn) {
     const int W = e->W, bc = e->bc;
     cudaStream_t st = e->st;
     RGF_CUDA_TRY(cudaMemcpyAsync(e->d_tab, e->h_tab, sizeof(SlotTab) * W, cudaMemcpyHostToDevice, st));
@@ -265,21 +280,21 @@ rgf_status engine_issue(Engine* e, bool all, int n_nf, int n_first, int n_last, 
     const int* d_first = d_act + 2 * W;
     const int* d_last = d_act + 3 * W;
     const int* d_refill = d_act + 4 * W;
-    if (all || n_refill)
+    if (all || n.n_refill)
         RGF_TRY(engine_refill(W, bc, e->d_tab, d_refill, e->U(16), e->U(0), e->dec_err, e->dec_flags, e->slot_err,
                               e->slot_flags, st));
-    float4 *sigL = e->U(0), *sigR = e->U(1), *gamL = e->U(2), *gamR = e->U(3);
-    float4 *gi = e->U(4), *P = e->U(5), *M = e->U(6), *Lt = e->U(7), *Ut = e->U(8);
-    float4 *G = e->U(11), *Xt = e->U(12), *Yt = e->U(13), *Rs = e->U(14);
-    SlotMasks mk{d_act, d_nf, d_first, d_last, d_refill};
-    RGF_TRY(engine_form_step(W, bc, e->d_tab, mk, sigL, sigR, M, Ut, Lt, st));
+    float4 *sigL = e->U(0), *sigR = e->U(1);
+    float4 *gi = e->U(4), *P = e->U(5), *M = e->U(6), *Rs = e->U(14);
+    // M only (nf = nullptr): tau and tau' go straight to their slices below.
+    SlotMasks mk{d_act, nullptr, d_first, d_last, d_refill};
+    RGF_TRY(engine_form_step(W, bc, e->d_tab, mk, sigL, sigR, M, nullptr, nullptr, st));
     Ctx c = engine_ctx(e, e->slot_err, e->slot_flags);
     c.graph = all;
-    if (all || n_nf) {
+    if (all || n.n_nf) {
         RGF_TRY(sliceA(c, W, 0, gi, d_nf));
-        RGF_TRY(sliceB(c, W, 0, Ut, d_nf));
+        RGF_TRY(form_slice_cols_dag_tab(W, bc, e->d_tab, d_nf, e->ms.sb[0], e->ms.Kp, st));
         RGF_TRY(mm(c, W, 0, 0, -1.0f, nullptr, 0, P, d_nf));  // P = -g tau'
-        RGF_TRY(sliceA(c, W, 0, Lt, d_nf));
+        RGF_TRY(form_slice_rows_tab(W, bc, e->d_tab, d_nf, e->ms.sa[0], e->ms.Kp, st));
         RGF_TRY(sliceB(c, W, 0, P, d_nf));
         RGF_TRY(mm(c, W, 0, 0, 1.0f, M, 0, M, d_nf));  // M += tau P
         RGF_TRY(sliceA(c, W, 1, Q, d_nf));
@@ -287,21 +302,67 @@ rgf_status engine_issue(Engine* e, bool all, int n_nf, int n_first, int n_last, 
     }
     // Slots on their first layer start the chain with Q = I in the next
     // step's Q buffer.
-    if (all || n_first) RGF_TRY(set_identity_masked_dfc(W, bc, Qn, d_first, st));
-    RGF_TRY(inv_mixed(c, W, W, M, gi, Rs, d_act, e->slot_flags));
-    if (all || n_last) {
-        RGF_TRY(sliceA(c, W, 0, Qn, d_last));
-        RGF_TRY(sliceB(c, W, 0, gi, d_last));
-        RGF_TRY(mm(c, W, 0, 0, 1.0f, nullptr, 0, G, d_last));  // G_{0,N-1} = Q g
-        RGF_TRY(sliceA(c, W, 0, gamL, d_last));
-        RGF_TRY(sliceB(c, W, 0, G, d_last));
-        RGF_TRY(mm(c, W, 0, 0, 1.0f, nullptr, 0, Xt, d_last));
-        RGF_TRY(sliceA(c, W, 0, G, d_last));
-        RGF_TRY(sliceB(c, W, 0, gamR, d_last));
-        RGF_TRY(mm(c, W, 0, 0, 1.0f, nullptr, 0, Yt, d_last));
-        RGF_TRY(trace_masked_dfc(W, bc, Xt, Yt, d_last, e->slot_T, st));
-        RGF_TRY(engine_finish(W, e->d_tab, d_last, e->slot_T, e->slot_err, e->slot_flags, st));
+    if (all || n.n_first) RGF_TRY(set_identity_masked_dfc(W, bc, Qn, d_first, st));
+    RGF_TRY(inv_mixed_steps(c, W, W, M, gi, Rs, d_act, e->slot_flags, 0, 2));
+    RGF_CUDA_TRY(cudaMemcpyAsync(e->ms.h_more, e->ms.more_count, sizeof(int), cudaMemcpyDeviceToHost, st));
+    return RGF_OK;
+}
+
+rgf_status engine_tail(Engine* e, bool all) {
+    const int W = e->W;
+    Ctx c = engine_ctx(e, e->slot_err, e->slot_flags);
+    c.graph = all;
+    return inv_mixed_steps(c, W, W, e->U(6), e->U(4), e->U(14), e->d_masks, e->slot_flags, 2, c.ns_steps);
+}
+
+rgf_status engine_back(Engine* e, bool all, const StepCounts& n, float4* Qn) {
+    const int W = e->W, bc = e->bc;
+    cudaStream_t st = e->st;
+    if (!(all || n.n_last)) return RGF_OK;
+    const int* d_last = e->d_masks + 3 * W;
+    float4 *gamL = e->U(2), *gamR = e->U(3), *gi = e->U(4);
+    float4 *G = e->U(11), *Xt = e->U(12), *Yt = e->U(13);
+    Ctx c = engine_ctx(e, e->slot_err, e->slot_flags);
+    c.graph = all;
+    RGF_TRY(sliceA(c, W, 0, Qn, d_last));
+    RGF_TRY(sliceB(c, W, 0, gi, d_last));
+    RGF_TRY(mm(c, W, 0, 0, 1.0f, nullptr, 0, G, d_last));  // G_{0,N-1} = Q g
+    RGF_TRY(sliceA(c, W, 0, gamL, d_last));
+    RGF_TRY(sliceB(c, W, 0, G, d_last));
+    RGF_TRY(mm(c, W, 0, 0, 1.0f, nullptr, 0, Xt, d_last));
+    RGF_TRY(sliceA(c, W, 0, G, d_last));
+    RGF_TRY(sliceB(c, W, 0, gamR, d_last));
+    RGF_TRY(mm(c, W, 0, 0, 1.0f, nullptr, 0, Yt, d_last));
+    RGF_TRY(trace_masked_dfc(W, bc, Xt, Yt, d_last, e->slot_T, st));
+    RGF_TRY(engine_finish(W, e->d_tab, d_last, e->slot_T, e->slot_err, e->slot_flags, st));
+    return RGF_OK;
+}
+
+// Capture (once) and launch one part of the step as a graph.
+template <typename F>
+rgf_status run_graph(Engine* e, cudaGraphExec_t& gx, F issue) {
+    cudaStream_t st = e->st;
+    if (!gx) {
+        RGF_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        rgf_status s = issue();
+        cudaGraph_t g = nullptr;
+        cudaError_t ce = cudaStreamEndCapture(st, &g);
+        if (s != RGF_OK || ce != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            if (s == RGF_OK) set_error("step capture failed: %s", cudaGetErrorString(ce));
+            return s != RGF_OK ? s : RGF_E_CUDA;
+        }
+        ce = cudaGraphInstantiate(&gx, g, 0);
+        cudaGraphDestroy(g);
+        if (ce != cudaSuccess) {
+            gx = nullptr;
+            cudaGetLastError();
+            set_error("step graph instantiation failed: %s", cudaGetErrorString(ce));
+            return RGF_E_CUDA;
+        }
     }
+    RGF_CUDA_TRY(cudaGraphLaunch(gx, st));
     return RGF_OK;
 }
 
@@ -313,7 +374,7 @@ rgf_status engine_step(Engine* e) {
     int* first = act + 2 * W;
     int* last = act + 3 * W;
     int* refill = act + 4 * W;
-    int n_nf = 0, n_first = 0, n_last = 0, n_refill = 0;
+    StepCounts n;
     for (int s = 0; s < W; ++s) {
         const Engine::Slot& sl = e->slots[s];
         SlotTab& t = e->h_tab[s];
@@ -328,10 +389,10 @@ rgf_status engine_step(Engine* e) {
         first[s] = l == 0;
         nf[s] = l > 0;
         last[s] = l == N - 1;
-        n_nf += nf[s];
-        n_first += first[s];
-        n_last += last[s];
-        n_refill += refill[s];
+        n.n_nf += nf[s];
+        n.n_first += first[s];
+        n.n_last += last[s];
+        n.n_refill += refill[s];
         t.Sii = r->Sd(l);
         t.Hii = r->Hd(l);
         t.Sl = l > 0 ? r->Sl(l) : nullptr;
@@ -347,33 +408,26 @@ rgf_status engine_step(Engine* e) {
     float4* Q = e->U(9 + e->parity);
     float4* Qn = e->U(10 - e->parity);
     // The first two steps run directly (one-time set-up calls happen there);
-    // later steps replay the captured sequence of their parity.
-    if (!e->graphs || e->steps < 2) {
-        RGF_TRY(engine_issue(e, e->graphs, n_nf, n_first, n_last, n_refill, Q, Qn));
-    } else {
-        cudaGraphExec_t& gx = e->gx[e->parity];
-        if (!gx) {
-            RGF_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-            rgf_status s = engine_issue(e, true, n_nf, n_first, n_last, n_refill, Q, Qn);
-            cudaGraph_t g = nullptr;
-            cudaError_t ce = cudaStreamEndCapture(st, &g);
-            if (s != RGF_OK || ce != cudaSuccess) {
-                if (g) cudaGraphDestroy(g);
-                cudaGetLastError();
-                if (s == RGF_OK) set_error("step capture failed: %s", cudaGetErrorString(ce));
-                return s != RGF_OK ? s : RGF_E_CUDA;
-            }
-            ce = cudaGraphInstantiate(&gx, g, 0);
-            cudaGraphDestroy(g);
-            if (ce != cudaSuccess) {
-                gx = nullptr;
-                cudaGetLastError();
-                set_error("step graph instantiation failed: %s", cudaGetErrorString(ce));
-                return RGF_E_CUDA;
-            }
-        }
-        RGF_CUDA_TRY(cudaGraphLaunch(gx, st));
+    // later steps replay the captured parts of their parity.
+    const bool graph = e->graphs && e->steps >= 2;
+    const bool all = e->graphs;
+    const int par = e->parity;
+    if (graph)
+        RGF_TRY(run_graph(e, e->gx[par], [&] { return engine_front(e, true, n, Q, Qn); }));
+    else
+        RGF_TRY(engine_front(e, all, n, Q, Qn));
+    // Newton-Schulz steps beyond the second only when an entry needs them.
+    RGF_CUDA_TRY(cudaStreamSynchronize(st));
+    if (e->sv->opt.ns_steps > 2 && *e->ms.h_more > 0) {
+        if (graph)
+            RGF_TRY(run_graph(e, e->gx_tail, [&] { return engine_tail(e, true); }));
+        else
+            RGF_TRY(engine_tail(e, all));
     }
+    if (graph)
+        RGF_TRY(run_graph(e, e->gx_back[par], [&] { return engine_back(e, true, n, Qn); }));
+    else
+        RGF_TRY(engine_back(e, all, n, Qn));
     e->parity ^= 1;
     long long acc = 0;
     RGF_CUDA_TRY(cudaMemcpyAsync(&acc, e->ms.reseed_acc, sizeof(acc), cudaMemcpyDeviceToHost, st));
