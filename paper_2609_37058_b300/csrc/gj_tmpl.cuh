@@ -126,6 +126,20 @@ static __global__ void __launch_bounds__(256) k_gj_update_f32(int m, int n, int 
     const float2* Ab = A + (long)bi * sA;
     const float2* Bb = B + (long)bi * sB;
     const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+    float2* Cb = C + (long)bi * sC;
+    // The accumulators start from C: its loads are issued first and are in
+    // flight while A and B are staged.
+    float2 acc[8][4];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int r = m0 + ty + 16 * i;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int c = n0 + tx + 16 * j;
+            acc[i][j] = (r < m && c < n) ? Cb[(long)r * ldc + c] : make_float2(0.f, 0.f);
+        }
+    }
     for (int i = tid; i < GU_BM * K; i += 256) {
         const int r = i / K, k = i - r * K;
         As[r * GU_AP + k] = (m0 + r < m) ? Ab[(long)(m0 + r) * K + k] : make_float2(0.f, 0.f);
@@ -135,12 +149,6 @@ static __global__ void __launch_bounds__(256) k_gj_update_f32(int m, int n, int 
         Bs[k * GU_BN + c] = (n0 + c < n) ? Bb[(long)k * ldc + n0 + c] : make_float2(0.f, 0.f);
     }
     __syncthreads();
-    const int tx = tid & 15, ty = tid >> 4;
-    float2 acc[8][4];
-#pragma unroll
-    for (int i = 0; i < 8; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
     for (int k = 0; k < K; ++k) {
         float2 a[8], b[4];
 #pragma unroll
@@ -152,7 +160,6 @@ static __global__ void __launch_bounds__(256) k_gj_update_f32(int m, int n, int 
 #pragma unroll
             for (int j = 0; j < 4; ++j) cfma(acc[i][j], a[i], b[j]);
     }
-    float2* Cb = C + (long)bi * sC;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         const int r = m0 + ty + 16 * i;
@@ -161,10 +168,7 @@ static __global__ void __launch_bounds__(256) k_gj_update_f32(int m, int n, int 
         for (int j = 0; j < 4; ++j) {
             const int c = n0 + tx + 16 * j;
             if (c >= n || (c >= skip0 && c < skip1)) continue;
-            float2 v = Cb[(long)r * ldc + c];
-            v.x += acc[i][j].x;
-            v.y += acc[i][j].y;
-            Cb[(long)r * ldc + c] = v;
+            Cb[(long)r * ldc + c] = acc[i][j];
         }
     }
 }

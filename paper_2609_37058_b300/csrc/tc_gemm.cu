@@ -10,7 +10,8 @@
 //     M = 128, N = BN, K = 16) for the 21 slice pairs (i, j), i + j <= 5,
 //     accumulating pair (i, j) in TMEM accumulator min(i + j, 4) (five
 //     accumulators x BN columns of the 512 allocated);
-//   * four warps read the accumulators back with tcgen05.ld and combine
+//   * eight warps (two per TMEM lane quarter, alternating 16-column chunks)
+//     read the accumulators back with tcgen05.ld and combine
 //     the groups with exact FP32 TwoSums into double-float results (or, for
 //     the FP64 variant, into an FP32 expansion rounded once to FP64), apply
 //     the epilogue (sign, addend, identity) and store.
@@ -203,7 +204,7 @@ struct TcArgs {
 };
 
 template <int NSL, int NGRP, int BN, bool OUT64, int BK, int PL>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(256, 1)
     k_oz_tc(TcArgs g, const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB) {
     using Cfg = TcCfg<NSL, NGRP, BN, BK>;
     constexpr int S = Cfg::STAGES;
@@ -297,10 +298,13 @@ __global__ void __launch_bounds__(128, 1)
     __syncwarp();
     tc_fence_after();
     if (done) {
-        const int r = m0 + warp * 32 + lane;
-        const uint32_t trow = taddr + ((uint32_t)(warp * 32) << 16);
+        // Eight warps: warp w reads TMEM lanes 32 (w % 4) .. +31 (its row
+        // quarter) and takes every other 16-column chunk, starting at w / 4.
+        const int quad = warp & 3;
+        const int r = m0 + quad * 32 + lane;
+        const uint32_t trow = taddr + ((uint32_t)(quad * 32) << 16);
 #pragma unroll 1
-        for (int q = 0; q < BN / 16; ++q) {
+        for (int q = warp >> 2; q < BN / 16; q += 2) {
             float v[NGRP][16];
 #pragma unroll
             for (int gq = 0; gq < NGRP; ++gq) tmem_ld16(trow + gq * BN + q * 16, v[gq]);
@@ -426,7 +430,7 @@ static rgf_status launch_tc(const TcArgs& g, cudaStream_t st) {
     const bool timed = gemm_timing_enabled() && g.active == nullptr;
     cudaEvent_t ev = nullptr;
     if (timed) gemm_timing_before(st, &ev);
-    k_oz_tc<NSL, NGRP, BN, OUT64, BK, PL><<<grid, 128, Cfg::SMEM, st>>>(g, ta, tb);
+    k_oz_tc<NSL, NGRP, BN, OUT64, BK, PL><<<grid, 256, Cfg::SMEM, st>>>(g, ta, tb);
     RGF_LAUNCH_CHECK();
     if (timed) {
         // NSL(NSL+1)/2 slice-pair real products of M = m, N = 2n, K = 2k per batch entry.
