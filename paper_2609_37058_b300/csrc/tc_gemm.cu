@@ -141,11 +141,26 @@ __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
+// Exact FP32 -> FP64 widening on the integer pipe for normal numbers,
+// infinities and NaNs (rebias the exponent, shift the mantissa); zeros and
+// subnormals take the hardware conversion.  The FP64 pipe of this GPU is
+// narrow and the seven-slice epilogue is bound by it.
+__device__ __forceinline__ double f2d(float x) {
+    const uint32_t u = __float_as_uint(x);
+    const uint32_t e = (u >> 23) & 0xffu;
+    if (e == 0) return (double)x;
+    const uint64_t sign = (uint64_t)(u >> 31) << 63;
+    const uint64_t exp = (e == 0xffu) ? 0x7ffull : (uint64_t)(e + 896u);
+    const uint64_t man = (uint64_t)(u & 0x7fffffu) << 29;
+    return __longlong_as_double((long long)(sign | (exp << 52) | man));
+}
+
 // FP64 value of the sum of NGRP group values: a TwoSum cascade in FP32
 // leaves the rounded sum s and the exact errors e_1..e_{NGRP-1}; those are
 // summed again with TwoSum into t and a last correction f, and only
-// s + (t + f) is formed in FP64 (three conversions and two FP64 additions
-// per output instead of one of each per group: the FP64 pipe is narrow).
+// s + (t + f) is formed in FP64 (three widenings, done on the integer pipe,
+// and two FP64 additions per output instead of a conversion and an addition
+// per group: the FP64 pipe is narrow).
 template <int NGRP>
 __device__ __forceinline__ double sum_groups_f64(const float (&v)[NGRP][16], int idx) {
     float s = v[0][idx];
@@ -163,7 +178,7 @@ __device__ __forceinline__ double sum_groups_f64(const float (&v)[NGRP][16], int
         t = r.x;
         f += r.y;
     }
-    return (double)s + ((double)t + (double)f);
+    return f2d(s) + (f2d(t) + f2d(f));
 }
 
 // Double-float value of the group sums: groups 0..NGRP-2 through exact
