@@ -7,7 +7,10 @@
 // pattern with 64-bit integer arithmetic (no FP64 arithmetic): Y =
 // round(|x| 2^(55-e)) < 2^55, then base-256 digits from the bottom with a
 // carry whenever a digit exceeds 127.  Rounding error: 2^-56 of 2^e.
+#include <atomic>
+
 #include "mixed.h"
+#include "slice_strip.cuh"
 
 namespace rgf {
 
@@ -90,8 +93,9 @@ __global__ void __launch_bounds__(256) k_slice_rows_f64(int m, int k, const doub
     }
 }
 
-// One CTA per strip of 32 columns: column exponents first, then 32 x 32
-// tiles through shared memory (layout as the double-float column slicer).
+// Two-pass column slicer for strips that do not fit in shared memory: one
+// CTA per strip of 32 columns, column exponents first, then 32 x 32 tiles
+// through shared memory (layout as the double-float column slicer).
 __global__ void __launch_bounds__(256) k_slice_cols_f64(int k, int n, const double2* __restrict__ B, long sB,
                                                         __nv_bfloat16* __restrict__ out, int Kp,
                                                         const int* __restrict__ active) {
@@ -161,9 +165,38 @@ rgf_status slice_rows_f64(int batch, int m, int k, const double2* A, long sA, __
     return RGF_OK;
 }
 
+struct F64Strip {
+    static constexpr int kMinBlocks = 3;
+    using T = double2;
+    using M = double;
+    static constexpr int NS = kSlicesHP;
+    __device__ static T zero() { return make_double2(0.0, 0.0); }
+    __device__ static M amax(const T& v) { return fmax(fabs(v.x), fabs(v.y)); }
+    __device__ static M vmax(M a, M b) { return fmax(a, b); }
+    __device__ static M shfl_xor(M v, int off) { return __shfl_xor_sync(0xffffffffu, v, off); }
+    __device__ static int expo(M m) { return exp_above_f64(m); }
+    __device__ static void split(const T& v, int e, float* sr, float* si) {
+        digits7(v.x, e, sr);
+        digits7(v.y, e, si);
+    }
+};
+
 rgf_status slice_cols_f64(int batch, int k, int n, const double2* B, long sB, __nv_bfloat16* out, int Kp,
                           const int* active, cudaStream_t st) {
     if (batch <= 0) return RGF_OK;
+    if (strip_fits(k)) {
+        static std::atomic<bool> attr{false};
+        if (!attr.load()) {
+            // Idempotent: threads that race here all set the same value.
+            RGF_CUDA_TRY(cudaFuncSetAttribute(k_slice_cols_strip<F64Strip>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, kStripMaxSmem));
+            attr.store(true);
+        }
+        k_slice_cols_strip<F64Strip><<<dim3(ceil_div(n, kStripCols), batch), kStripCols * 32, strip_smem_bytes(k),
+                                       st>>>(k, n, B, sB, out, Kp, active);
+        RGF_LAUNCH_CHECK();
+        return RGF_OK;
+    }
     k_slice_cols_f64<<<dim3(ceil_div(n, 32), batch), 256, 0, st>>>(k, n, B, sB, out, Kp, active);
     RGF_LAUNCH_CHECK();
     return RGF_OK;

@@ -6,6 +6,7 @@
 #include "df.cuh"
 #include "engine.h"
 #include "mixed.h"
+#include "slice_strip.cuh"
 
 namespace rgf {
 
@@ -283,10 +284,12 @@ rgf_status slice_rows(int batch, int m, int k, const float4* A, long sA, __nv_bf
     return RGF_OK;
 }
 
-// One CTA per strip of 32 columns of one batch entry: first the column
-// maxima (exponents) over all k rows, then 32 (j) x 32 (c) tiles through
-// shared memory so that both the df reads (along c) and the slice writes
-// (along j) are coalesced.  The second pass re-reads the strip from L2.
+// Two-pass column slicer for operands whose strip does not fit in shared
+// memory (k above ~1400): one CTA per strip of 32 columns of one batch
+// entry, first the column maxima (exponents) over all k rows, then 32 (j) x
+// 32 (c) tiles through shared memory so that both the df reads (along c) and
+// the slice writes (along j) are coalesced.  The second pass re-reads the
+// strip.
 __global__ void __launch_bounds__(256) k_slice_cols(int k, int n, const float4* __restrict__ B, long sB,
                                                     __nv_bfloat16* __restrict__ out, int Kp,
                                                     const int* __restrict__ active) {
@@ -346,9 +349,38 @@ __global__ void __launch_bounds__(256) k_slice_cols(int k, int n, const float4* 
     }
 }
 
+struct DfStrip {
+    static constexpr int kMinBlocks = 4;
+    using T = float4;
+    using M = float;
+    static constexpr int NS = kSlices;
+    __device__ static T zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+    __device__ static M amax(const T& v) { return fmaxf(fabsf(v.x), fabsf(v.z)); }
+    __device__ static M vmax(M a, M b) { return fmaxf(a, b); }
+    __device__ static M shfl_xor(M v, int off) { return __shfl_xor_sync(0xffffffffu, v, off); }
+    __device__ static int expo(M m) { return exp_above(m); }
+    __device__ static void split(const T& v, int e, float* sr, float* si) {
+        slice6(v.x, v.y, e, sr);
+        slice6(v.z, v.w, e, si);
+    }
+};
+
 rgf_status slice_cols(int batch, int k, int n, const float4* B, long sB, __nv_bfloat16* out, int Kp,
                       const int* active, cudaStream_t st) {
     if (batch <= 0) return RGF_OK;
+    if (strip_fits(k)) {
+        static std::atomic<bool> attr{false};
+        if (!attr.load()) {
+            // Idempotent: threads that race here all set the same value.
+            RGF_CUDA_TRY(cudaFuncSetAttribute(k_slice_cols_strip<DfStrip>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, kStripMaxSmem));
+            attr.store(true);
+        }
+        k_slice_cols_strip<DfStrip><<<dim3(ceil_div(n, kStripCols), batch), kStripCols * 32, strip_smem_bytes(k),
+                                      st>>>(k, n, B, sB, out, Kp, active);
+        RGF_LAUNCH_CHECK();
+        return RGF_OK;
+    }
     k_slice_cols<<<dim3(ceil_div(n, 32), batch), 256, 0, st>>>(k, n, B, sB, out, Kp, active);
     RGF_LAUNCH_CHECK();
     return RGF_OK;
