@@ -74,6 +74,9 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
 __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
@@ -218,6 +221,105 @@ struct TcArgs {
     int skip_first_chunk;
 };
 
+// Output element: double-float complex (float4) or FP64 complex (double2).
+template <bool OUT64>
+using OutT = typename std::conditional<OUT64, double2, float4>::type;
+
+// The 8 complex values (16 real accumulator columns) one lane holds for one
+// row: group sums combined, sign applied.
+template <int NGRP, bool OUT64>
+__device__ __forceinline__ void combine_chunk(const TcArgs& g, const float (&v)[NGRP][16], OutT<OUT64> (&res)[8]) {
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        if constexpr (OUT64) {
+            double re = sum_groups_f64<NGRP>(v, 2 * t);
+            double im = sum_groups_f64<NGRP>(v, 2 * t + 1);
+            if (g.alpha < 0.0f) {
+                re = -re;
+                im = -im;
+            }
+            res[t] = make_double2(re, im);
+        } else {
+            float2 re = combine_df<NGRP>(v, 2 * t);
+            float2 im = combine_df<NGRP>(v, 2 * t + 1);
+            if (g.alpha < 0.0f) {
+                re = df_neg(re);
+                im = df_neg(im);
+            }
+            res[t] = cdf(re, im);
+        }
+    }
+}
+
+// Addend and identity of those values and their store: row r, columns from cb.
+template <bool OUT64>
+__device__ __forceinline__ void finish_chunk(const TcArgs& g, const OutT<OUT64> (&res)[8], int bi, int r, int cb) {
+    if (r >= g.m) return;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        const int c = cb + t;
+        if (c >= g.n) continue;
+        const long o = (long)bi * g.sC + (long)r * g.n + c;
+        if constexpr (OUT64) {
+            double re = res[t].x, im = res[t].y;
+            if (g.D) {
+                const double2 d = reinterpret_cast<const double2*>(g.D)[(long)bi * g.sD + (long)r * g.n + c];
+                re += d.x;
+                im += d.y;
+            }
+            if (g.add_identity && r == c) re += 1.0;
+            reinterpret_cast<double2*>(g.C)[o] = make_double2(re, im);
+        } else {
+            float2 re = re_of(res[t]), im = im_of(res[t]);
+            if (g.D) {
+                const float4 d = reinterpret_cast<const float4*>(g.D)[(long)bi * g.sD + (long)r * g.n + c];
+                re = df_add(re, re_of(d));
+                im = df_add(im, im_of(d));
+            }
+            if (g.add_identity && r == c) re = df_add(re, make_float2(1.0f, 0.0f));
+            reinterpret_cast<float4*>(g.C)[o] = cdf(re, im);
+        }
+    }
+}
+
+template <int NGRP, bool OUT64>
+__device__ __forceinline__ void store_chunk(const TcArgs& g, const float (&v)[NGRP][16], int bi, int r, int cb) {
+    OutT<OUT64> res[8];
+    combine_chunk<NGRP, OUT64>(g, v, res);
+    finish_chunk<OUT64>(g, res, bi, r, cb);
+}
+
+// MMAs of one K chunk in stage buffer st: the slice pairs (i, j), i + j <=
+// NSL - 1, into accumulator min(i + j, NGRP - 1).  first: the tile's first
+// chunk (each accumulator is overwritten by its first product).
+template <int NSL, int NGRP, int BN, int BK>
+__device__ __forceinline__ void mma_chunk(const unsigned char* st, uint32_t taddr, bool first) {
+    using Cfg = TcCfg<NSL, NGRP, BN, BK>;
+    // Descriptors of the stage's first A and B tiles; a tile at byte offset
+    // o from them has the descriptor + o / 16 (the start-address field is
+    // the low 14 bits of address / 16, and shared addresses stay below
+    // 256 KB, so the addition never carries out of it).
+    const uint64_t da = desc_sw(smem_u32(st), Cfg::SWZ, Cfg::SBO);
+    const uint64_t db = desc_sw(smem_u32(st + NSL * Cfg::ATILE), Cfg::SWZ, Cfg::SBO);
+    uint32_t started = 0;
+#pragma unroll
+    for (int i = 0; i < NSL; ++i) {
+#pragma unroll
+        for (int j = 0; j < NSL; ++j) {
+            if (i + j > NSL - 1) continue;
+            const int grp = (i + j) < (NGRP - 1) ? (i + j) : (NGRP - 1);
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk) {
+                const uint64_t ad = da + (uint64_t)((i * Cfg::ATILE + kk * 32) >> 4);
+                const uint64_t bd = db + (uint64_t)((j * Cfg::BTILE + kk * 32) >> 4);
+                const uint32_t acc = (!first || (started >> grp) & 1u) ? 1u : 0u;
+                umma(taddr + (uint32_t)(grp * BN), ad, bd, Cfg::IDESC, acc);
+                started |= 1u << grp;
+            }
+        }
+    }
+}
+
 template <int NSL, int NGRP, int BN, bool OUT64, int BK, int PL>
 __global__ void __launch_bounds__(256, 1)
     k_oz_tc(TcArgs g, const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB) {
@@ -279,25 +381,7 @@ __global__ void __launch_bounds__(256, 1)
                 break;
             }
             tc_fence_after();
-            unsigned char* st = base + s * Cfg::STAGE;
-            const uint32_t a0 = smem_u32(st), b0 = smem_u32(st + NSL * Cfg::ATILE);
-            uint32_t started = 0;
-#pragma unroll
-            for (int i = 0; i < NSL; ++i) {
-#pragma unroll
-                for (int j = 0; j < NSL; ++j) {
-                    if (i + j > NSL - 1) continue;
-                    const int grp = (i + j) < (NGRP - 1) ? (i + j) : (NGRP - 1);
-#pragma unroll
-                    for (int kk = 0; kk < BK / 16; ++kk) {
-                        const uint64_t ad = desc_sw(a0 + i * Cfg::ATILE + kk * 32, Cfg::SWZ, Cfg::SBO);
-                        const uint64_t bd = desc_sw(b0 + j * Cfg::BTILE + kk * 32, Cfg::SWZ, Cfg::SBO);
-                        const uint32_t acc = (kc > 0 || (started >> grp) & 1u) ? 1u : 0u;
-                        umma(taddr + (uint32_t)(grp * BN), ad, bd, Cfg::IDESC, acc);
-                        started |= 1u << grp;
-                    }
-                }
-            }
+            mma_chunk<NSL, NGRP, BN, BK>(base + s * Cfg::STAGE, taddr, kc == 0);
             umma_commit(smem_u32(&bars[S + s]));
         }
         umma_commit(smem_u32(&bars[2 * S]));
@@ -324,44 +408,7 @@ __global__ void __launch_bounds__(256, 1)
 #pragma unroll
             for (int gq = 0; gq < NGRP; ++gq) tmem_ld16(trow + gq * BN + q * 16, v[gq]);
             tmem_ld_wait();
-            if (r < g.m) {
-                const int c0 = (n0 + q * 16) >> 1;
-#pragma unroll
-                for (int t = 0; t < 8; ++t) {
-                    const int c = c0 + t;
-                    if (c >= g.n) continue;
-                    const long o = (long)bi * g.sC + (long)r * g.n + c;
-                    if constexpr (OUT64) {
-                        double re = sum_groups_f64<NGRP>(v, 2 * t);
-                        double im = sum_groups_f64<NGRP>(v, 2 * t + 1);
-                        if (g.alpha < 0.0f) {
-                            re = -re;
-                            im = -im;
-                        }
-                        if (g.D) {
-                            const double2 d = reinterpret_cast<const double2*>(g.D)[(long)bi * g.sD + (long)r * g.n + c];
-                            re += d.x;
-                            im += d.y;
-                        }
-                        if (g.add_identity && r == c) re += 1.0;
-                        reinterpret_cast<double2*>(g.C)[o] = make_double2(re, im);
-                    } else {
-                        float2 re = combine_df<NGRP>(v, 2 * t);
-                        float2 im = combine_df<NGRP>(v, 2 * t + 1);
-                        if (g.alpha < 0.0f) {
-                            re = df_neg(re);
-                            im = df_neg(im);
-                        }
-                        if (g.D) {
-                            const float4 d = reinterpret_cast<const float4*>(g.D)[(long)bi * g.sD + (long)r * g.n + c];
-                            re = df_add(re, re_of(d));
-                            im = df_add(im, im_of(d));
-                        }
-                        if (g.add_identity && r == c) re = df_add(re, make_float2(1.0f, 0.0f));
-                        reinterpret_cast<float4*>(g.C)[o] = cdf(re, im);
-                    }
-                }
-            }
+            store_chunk<NGRP, OUT64>(g, v, bi, r, (n0 + q * 16) >> 1);
         }
     }
     tc_fence_before();
@@ -369,6 +416,205 @@ __global__ void __launch_bounds__(256, 1)
     if (!done && tid == 0) {
         // Drain TMA copies that may still be in flight before the CTA exits.
         for (int s = 0; s < S; ++s) mbar_wait(smem_u32(&bars[s]), 0, status, 0x8, g.wait_ns);
+    }
+    __syncthreads();
+    if (warp == 1) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(TC_TMEM_COLS)
+                     : "memory");
+    }
+}
+
+// Persistent form: one CTA per SM walks the tiles t = blockIdx.x,
+// blockIdx.x + gridDim.x, ... (same tile order as the one-tile grid), with
+// warp 0 the TMA producer, warp 1 the MMA issuer and warps 2..9 the
+// epilogue (TMEM lane quarter warp % 4, alternate 16-column chunks).  The
+// stage ring and its phases run on across tiles, so the producer loads the
+// next tile's first chunks while the epilogue drains the accumulators, and
+// the MMA issuer starts the next tile as soon as every epilogue warp has
+// read and combined its chunks (the accumulators are single-buffered:
+// NGRP * BN of the 512 columns); addends and stores follow.
+template <int NSL, int NGRP, int BN, bool OUT64, int BK, int PL>
+__global__ void __launch_bounds__(320, 1)
+    k_oz_tc_p(TcArgs g, const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB) {
+    using Cfg = TcCfg<NSL, NGRP, BN, BK>;
+    constexpr int S = Cfg::STAGES;
+    constexpr int NQ = BN / 16;      // 16-column chunks of the tile
+    constexpr int NCH = (NQ + 1) / 2;  // chunks per epilogue warp (at most)
+    // Results of all chunks held in registers until the accumulators are
+    // released: only where they fit in the 168 registers a thread of a
+    // ten-warp CTA gets (the double-float tiles of width 64 and 96).
+    constexpr bool kDefer = !OUT64 && BN != 80;
+    static_assert(NQ >= 2, "every epilogue warp needs a chunk");
+    extern __shared__ __align__(1024) unsigned char smem_tc[];
+    unsigned char* base = (unsigned char*)(((uintptr_t)smem_tc + 1023) & ~(uintptr_t)1023);
+    // bars[0..S-1] full, bars[S..2S-1] empty, bars[2S] accumulators full,
+    // bars[2S+1] accumulators empty; then the TMEM slot and three words.
+    uint64_t* bars = reinterpret_cast<uint64_t*>(base + S * Cfg::STAGE);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * S + 2);
+    volatile int* s_fail = reinterpret_cast<volatile int*>(tmem_slot + 1);  // a role gave up on a wait
+    volatile int* s_issued = s_fail + 1;    // chunks whose loads were issued
+    volatile int* s_consumed = s_fail + 2;  // chunks the MMA issuer received
+    const uint32_t acc_full = smem_u32(&bars[2 * S]), acc_empty = smem_u32(&bars[2 * S + 1]);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int ntx = (2 * g.n + BN - 1) / BN, nty = (g.m + TC_BM - 1) / TC_BM;
+    const int ntiles = ntx * nty * g.batch;
+    const int nk = g.Kp / BK;
+    int* status = g.status;
+
+    if (tid == 0) {
+        for (int i = 0; i < 2 * S + 1; ++i) mbar_init(smem_u32(&bars[i]), 1);
+        mbar_init(acc_empty, 8);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        *s_fail = 0;
+        *s_issued = 0;
+        *s_consumed = 0;
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(TC_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t taddr = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- TMA producer
+            int gc = 0;
+            for (int t = blockIdx.x; t < ntiles && !*s_fail; t += gridDim.x) {
+                const int bx = t % ntx, by = (t / ntx) % nty, bi = t / (ntx * nty);
+                if (g.active && !g.active[bi]) continue;
+                bool ok = true;
+                for (int kc = 0; kc < nk; ++kc, ++gc) {
+                    const int s = gc % S;
+                    if (gc >= S && !mbar_wait(smem_u32(&bars[S + s]), ((gc / S) - 1) & 1, status, 0x1, g.wait_ns)) {
+                        ok = false;
+                        break;
+                    }
+                    *s_issued = gc + 1;
+                    if (gc == 0 && g.skip_first_chunk) continue;
+                    const uint32_t fb = smem_u32(&bars[s]);
+                    mbar_expect_tx(fb, Cfg::STAGE);
+                    unsigned char* st = base + s * Cfg::STAGE;
+#pragma unroll
+                    for (int sl = 0; sl < NSL; ++sl) {
+                        tma_load_3d(smem_u32(st + sl * Cfg::ATILE), &tmA, kc * BK, by * TC_BM, bi * PL + sl, fb);
+                        tma_load_3d(smem_u32(st + NSL * Cfg::ATILE + sl * Cfg::BTILE), &tmB, kc * BK, bx * BN,
+                                    bi * PL + sl, fb);
+                    }
+                }
+                if (!ok) {
+                    *s_fail = 1;
+                    break;
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer
+            int gc = 0, lt = 0;
+            for (int t = blockIdx.x; t < ntiles && !*s_fail; t += gridDim.x) {
+                const int bi = t / (ntx * nty);
+                if (g.active && !g.active[bi]) continue;
+                if (lt > 0 && !mbar_wait(acc_empty, (lt - 1) & 1, status, 0x2, g.wait_ns)) {
+                    *s_fail = 1;
+                    break;
+                }
+                tc_fence_after();
+                bool ok = true;
+                for (int kc = 0; kc < nk; ++kc, ++gc) {
+                    const int s = gc % S;
+                    if (!mbar_wait(smem_u32(&bars[s]), (gc / S) & 1, status, 0x2, g.wait_ns)) {
+                        ok = false;
+                        break;
+                    }
+                    *s_consumed = gc + 1;
+                    tc_fence_after();
+                    mma_chunk<NSL, NGRP, BN, BK>(base + s * Cfg::STAGE, taddr, kc == 0);
+                    umma_commit(smem_u32(&bars[S + s]));
+                }
+                if (!ok) *s_fail = 1;
+                // Committed also after a failure, so that the epilogue's wait ends.
+                umma_commit(acc_full);
+                if (!ok) break;
+                ++lt;
+            }
+        }
+    } else {
+        // ---------------- epilogue: TMEM -> registers -> result -> global
+        const int quad = warp & 3;
+        const int half = (warp - 2) >> 2;
+        const uint32_t trow = taddr + ((uint32_t)(quad * 32) << 16);
+        int lt = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+            const int bx = t % ntx, by = (t / ntx) % nty, bi = t / (ntx * nty);
+            if (g.active && !g.active[bi]) continue;
+            // One lane waits; the outcome is made warp-uniform because the
+            // TMEM loads below are warp-collective.
+            int ok_i = 0;
+            if (lane == 0) ok_i = (mbar_wait(acc_full, lt & 1, status, 0x4, g.wait_ns) && !*s_fail) ? 1 : 0;
+            if (__shfl_sync(0xffffffffu, ok_i, 0) == 0) break;
+            tc_fence_after();
+            const int r = by * TC_BM + quad * 32 + lane;
+            if constexpr (!kDefer) {
+#pragma unroll 1
+                for (int q = half; q < NQ; q += 2) {
+                    float v[NGRP][16];
+#pragma unroll
+                    for (int gq = 0; gq < NGRP; ++gq) tmem_ld16(trow + gq * BN + q * 16, v[gq]);
+                    tmem_ld_wait();
+                    if (q + 2 >= NQ) {
+                        // This warp's last chunk is in registers: release
+                        // the accumulators to the next tile's MMAs.
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(acc_empty);
+                    }
+                    store_chunk<NGRP, OUT64>(g, v, bi, r, (bx * BN + q * 16) >> 1);
+                }
+                ++lt;
+                continue;
+            }
+            // All of this warp's chunks are read and combined into registers
+            // before the accumulators are released; the addends are read and
+            // the results stored while the next tile's MMAs run.
+            OutT<OUT64> res[NCH][8];
+#pragma unroll
+            for (int k = 0; k < NCH; ++k) {
+                const int q = half + 2 * k;
+                if (q < NQ) {
+                    float v[NGRP][16];
+#pragma unroll
+                    for (int gq = 0; gq < NGRP; ++gq) tmem_ld16(trow + gq * BN + q * 16, v[gq]);
+                    tmem_ld_wait();
+                    if (q + 2 >= NQ) {
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(acc_empty);
+                    }
+                    combine_chunk<NGRP, OUT64>(g, v, res[k]);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < NCH; ++k) {
+                const int q = half + 2 * k;
+                if (q < NQ) finish_chunk<OUT64>(g, res[k], bi, r, (bx * BN + q * 16) >> 1);
+            }
+            ++lt;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0 && *s_fail) {
+        // Drain TMA copies that may still be in flight before the CTA exits:
+        // the chunks issued but not received by the MMA issuer (at most S,
+        // on distinct stages).
+        for (int c = *s_consumed; c < *s_issued; ++c)
+            mbar_wait(smem_u32(&bars[c % S]), (c / S) & 1, status, 0x8, g.wait_ns);
     }
     __syncthreads();
     if (warp == 1) {
@@ -418,6 +664,22 @@ static rgf_status encode_slices(CUtensorMap* map, const __nv_bfloat16* ptr, int 
 
 // PL: slice planes per batch entry in the buffers (>= NSL; the kernel reads
 // the NSL most significant).
+// Shared memory of a persistent CTA: at least 116 KB, so that no two CTAs
+// that allocate the whole TMEM share an SM (one would wait in tcgen05.alloc
+// until the other has finished all its tiles).
+template <int SMEM>
+constexpr int kPersistSmem = SMEM > 116 * 1024 ? SMEM : 116 * 1024;
+
+// Persistent tile loop (default) or one CTA per tile with
+// RGF_TC_PERSIST=0 in the environment (read once).
+static bool tc_persistent() {
+    static const bool on = [] {
+        const char* e = getenv("RGF_TC_PERSIST");
+        return !(e && e[0] == '0');
+    }();
+    return on;
+}
+
 template <int NSL, int NGRP, int BN, bool OUT64, int BK, int PL = NSL>
 static rgf_status launch_tc(const TcArgs& g, cudaStream_t st) {
     using Cfg = TcCfg<NSL, NGRP, BN, BK>;
@@ -438,14 +700,26 @@ static rgf_status launch_tc(const TcArgs& g, cudaStream_t st) {
         // Idempotent: threads that race here all set the same value.
         RGF_CUDA_TRY(cudaFuncSetAttribute(k_oz_tc<NSL, NGRP, BN, OUT64, BK, PL>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM));
+        RGF_CUDA_TRY(cudaFuncSetAttribute(k_oz_tc_p<NSL, NGRP, BN, OUT64, BK, PL>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, kPersistSmem<Cfg::SMEM>));
         attr.store(true);
     }
     dim3 grid(ceil_div(2L * g.n, BN), ceil_div(g.m, TC_BM), g.batch);
+    const long ntiles = (long)grid.x * grid.y * grid.z;
+    int dev = 0, nsm = 0;
+    RGF_CUDA_TRY(cudaGetDevice(&dev));
+    RGF_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const bool persistent = tc_persistent() && ntiles < 0x7fffffffL;
     // Only unmasked launches are timed: their work is exactly known.
     const bool timed = gemm_timing_enabled() && g.active == nullptr;
     cudaEvent_t ev = nullptr;
     if (timed) gemm_timing_before(st, &ev);
-    k_oz_tc<NSL, NGRP, BN, OUT64, BK, PL><<<grid, 256, Cfg::SMEM, st>>>(g, ta, tb);
+    if (persistent) {
+        const int nblk = (int)(ntiles < nsm ? ntiles : nsm);
+        k_oz_tc_p<NSL, NGRP, BN, OUT64, BK, PL><<<nblk, 320, kPersistSmem<Cfg::SMEM>, st>>>(g, ta, tb);
+    } else {
+        k_oz_tc<NSL, NGRP, BN, OUT64, BK, PL><<<grid, 256, Cfg::SMEM, st>>>(g, ta, tb);
+    }
     RGF_LAUNCH_CHECK();
     if (timed) {
         // NSL(NSL+1)/2 slice-pair real products of M = m, N = 2n, K = 2k per batch entry.

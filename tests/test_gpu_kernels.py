@@ -129,3 +129,29 @@ def test_tc_bounded_waits_report_and_recover(rgf):
     A, B = crand(rng, 2, 64, 64), crand(rng, 2, 64, 64)
     C = rgf.rgf_kernel_zgemm_mixed(A, B, core=0)
     assert np.all(np.abs(C - A @ B) <= mixed_bound(A, B))
+
+
+def test_persistent_and_per_tile_gemms_agree(rgf, tmp_path):
+    """The persistent tile loop and the one-CTA-per-tile form issue the same
+    products in the same order and combine them identically: their results
+    are bit-identical (the per-tile form is selected with RGF_TC_PERSIST=0,
+    read once per process, hence the child process)."""
+    import os
+    import subprocess
+    import sys
+    rng = np.random.default_rng(21)
+    A, B = crand(rng, 3, 200, 136), crand(rng, 3, 136, 176)
+    np.save(tmp_path / "A.npy", A)
+    np.save(tmp_path / "B.npy", B)
+    code = (
+        "import numpy as np, sys\n"
+        "from paper_2609_37058_b300 import rgf\n"
+        "d = sys.argv[1]\n"
+        "A, B = np.load(d + '/A.npy'), np.load(d + '/B.npy')\n"
+        "np.save(d + '/C.npy', rgf.rgf_kernel_zgemm_mixed(A, B, core=0))\n"
+        "np.save(d + '/H.npy', rgf.rgf_kernel_zgemm_hp(A, B))\n")
+    env = dict(os.environ, RGF_TC_PERSIST="0")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    subprocess.run([sys.executable, "-c", code, str(tmp_path)], env=env, cwd=root, check=True, timeout=600)
+    assert np.array_equal(rgf.rgf_kernel_zgemm_mixed(A, B, core=0), np.load(tmp_path / "C.npy"))
+    assert np.array_equal(rgf.rgf_kernel_zgemm_hp(A, B), np.load(tmp_path / "H.npy"))
