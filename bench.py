@@ -30,8 +30,8 @@ METRIC = "RGF energy-points/s (b=256, 500 layers), mixed vs FP64 at |dT|<=1e-6; 
 # was measured on; reported (scaled by the flops of the timed launches) only
 # while that source is unchanged.  Capture: batch 148, b = 256, tile 96
 # (profiles/k_oz_tc_b256_batch148.md).
-GEMM_TRAFFIC = (699.513344e6 + 137.784320e6, 21 * 2.0 * 256 * 512 * 512 * 148,
-                "83d4a668fbf8080168b8d56ffaefbae25ef964d579436d0ea1e8ec00b28831aa")
+GEMM_TRAFFIC = (702.694400e6 + 133.302016e6, 21 * 2.0 * 256 * 512 * 512 * 148,
+                "2a4a6e5c0d71374ee3f8f1a047933c9d23106129aeb1df71a1e38f111e6fd091")
 
 
 def parse():
@@ -442,7 +442,7 @@ def main():
         if GEMM_TRAFFIC is not None and GEMM_TRAFFIC[2] == tc_source_hash():
             traffic = GEMM_TRAFFIC[0] * (gemm_flops / gemm_n) / GEMM_TRAFFIC[1] if gemm_n else None
             # per launch, scaled from the captured launch by the flops ratio
-        roof = {"bound": "tensor", "kernel": "k_oz_tc (slice-product GEMM, tcgen05)", "achieved": achieved,
+        roof = {"bound": "tensor", "kernel": "k_oz_tc_p (persistent slice-product GEMM, tcgen05)", "achieved": achieved,
                 "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                 "peak_source": f"bf16_tflops_sustained of {peak_src}", "launches": gemm_n,
                 "avg_launch_ms": gemm_ms / max(gemm_n, 1),
