@@ -193,7 +193,7 @@ rgf_status slice_cols_f64(int batch, int k, int n, const double2* B, long sB, __
             attr.store(true);
         }
         k_slice_cols_strip<F64Strip><<<dim3(ceil_div(n, kStripCols), batch), kStripCols * 32, strip_smem_bytes(k),
-                                       st>>>(k, n, B, sB, out, Kp, active);
+                                       st>>>(k, n, B, sB, out, Kp, active, kSlicesHP);
         RGF_LAUNCH_CHECK();
         return RGF_OK;
     }

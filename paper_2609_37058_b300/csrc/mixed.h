@@ -41,15 +41,17 @@ inline int slice_pitch(int k) { return ((2 * k + 63) / 64) * 64; }
 
 // Slices of the left operand A (m x k complex, df):
 //   out[((bi*kSlices + s)*m + r)*Kp + 2j + {0,1}] = slice s of (Re, Im) A[r][j]
+// planes: how many of the slices (the most significant) are written; a
+// product that reads fewer slices (OzGemm::nsl) needs only those.
 rgf_status slice_rows(int batch, int m, int k, const float4* A, long sA, __nv_bfloat16* out, int Kp,
-                      const int* active, cudaStream_t st);
+                      const int* active, cudaStream_t st, int planes = kSlices);
 // Slices of the right operand B (k x n complex, df) in transposed,
 // complex-expanded form (2n rows of Kp):
 //   row 2c  : (Re B[j][c], -Im B[j][c]) at K positions (2j, 2j+1)
 //   row 2c+1: (Im B[j][c],  Re B[j][c])
 // so that one real GEMM gives Re C in real column 2c and Im C in 2c+1.
 rgf_status slice_cols(int batch, int k, int n, const float4* B, long sB, __nv_bfloat16* out, int Kp,
-                      const int* active, cudaStream_t st);
+                      const int* active, cudaStream_t st, int planes = kSlices);
 
 // Slices of the coupling blocks formed on the fly for W energies (entry =
 // energy, z = E[e] + i eta; S, H one b x b df block each):

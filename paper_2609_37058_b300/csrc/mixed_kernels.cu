@@ -51,7 +51,7 @@ __device__ __forceinline__ float warp_max(float v) {
 
 __global__ void __launch_bounds__(256) k_slice_rows(int m, int k, const float4* __restrict__ A, long sA,
                                                     __nv_bfloat16* __restrict__ out, int Kp,
-                                                    const int* __restrict__ active) {
+                                                    const int* __restrict__ active, int planes) {
     const int bi = blockIdx.y;
     if (active && !active[bi]) return;
     const int lane = threadIdx.x & 31;
@@ -72,6 +72,7 @@ __global__ void __launch_bounds__(256) k_slice_rows(int m, int k, const float4* 
         slice6(v.z, v.w, e, si);
 #pragma unroll
         for (int s = 0; s < kSlices; ++s) {
+            if (s >= planes) break;
             __nv_bfloat162 p;
             p.x = __float2bfloat16_rn(sr[s]);
             p.y = __float2bfloat16_rn(si[s]);
@@ -276,10 +277,10 @@ rgf_status form_slice_cols_dag(int W, int b, const double* E, double eta, const 
 }
 
 rgf_status slice_rows(int batch, int m, int k, const float4* A, long sA, __nv_bfloat16* out, int Kp,
-                      const int* active, cudaStream_t st) {
+                      const int* active, cudaStream_t st, int planes) {
     if (batch <= 0) return RGF_OK;
     dim3 grid(ceil_div(m, 8), batch);
-    k_slice_rows<<<grid, 256, 0, st>>>(m, k, A, sA, out, Kp, active);
+    k_slice_rows<<<grid, 256, 0, st>>>(m, k, A, sA, out, Kp, active, planes);
     RGF_LAUNCH_CHECK();
     return RGF_OK;
 }
@@ -292,7 +293,7 @@ rgf_status slice_rows(int batch, int m, int k, const float4* A, long sA, __nv_bf
 // strip.
 __global__ void __launch_bounds__(256) k_slice_cols(int k, int n, const float4* __restrict__ B, long sB,
                                                     __nv_bfloat16* __restrict__ out, int Kp,
-                                                    const int* __restrict__ active) {
+                                                    const int* __restrict__ active, int planes) {
     const int bi = blockIdx.y;
     if (active && !active[bi]) return;
     __shared__ float4 tile[32][33];
@@ -336,6 +337,7 @@ __global__ void __launch_bounds__(256) k_slice_cols(int k, int n, const float4* 
             slice6(v.z, v.w, e, si);
 #pragma unroll
             for (int s = 0; s < kSlices; ++s) {
+                if (s >= planes) break;
                 __nv_bfloat16* base = out + (((long)bi * kSlices + s) * rows) * Kp;
                 __nv_bfloat162 p0, p1;
                 p0.x = __float2bfloat16_rn(sr[s]);
@@ -366,7 +368,7 @@ struct DfStrip {
 };
 
 rgf_status slice_cols(int batch, int k, int n, const float4* B, long sB, __nv_bfloat16* out, int Kp,
-                      const int* active, cudaStream_t st) {
+                      const int* active, cudaStream_t st, int planes) {
     if (batch <= 0) return RGF_OK;
     if (strip_fits(k)) {
         static std::atomic<bool> attr{false};
@@ -377,11 +379,11 @@ rgf_status slice_cols(int batch, int k, int n, const float4* B, long sB, __nv_bf
             attr.store(true);
         }
         k_slice_cols_strip<DfStrip><<<dim3(ceil_div(n, kStripCols), batch), kStripCols * 32, strip_smem_bytes(k),
-                                      st>>>(k, n, B, sB, out, Kp, active);
+                                      st>>>(k, n, B, sB, out, Kp, active, planes);
         RGF_LAUNCH_CHECK();
         return RGF_OK;
     }
-    k_slice_cols<<<dim3(ceil_div(n, 32), batch), 256, 0, st>>>(k, n, B, sB, out, Kp, active);
+    k_slice_cols<<<dim3(ceil_div(n, 32), batch), 256, 0, st>>>(k, n, B, sB, out, Kp, active, planes);
     RGF_LAUNCH_CHECK();
     return RGF_OK;
 }

@@ -84,9 +84,10 @@ struct Ctx {
     bool graph = false;
 };
 
-// Slice A by rows into sa[ia], B by columns into sb[ib]; C = alpha A B (+ D) (+ I).
-rgf_status sliceA(const Ctx& c, int cnt, int ia, const float4* A, const int* act);
-rgf_status sliceB(const Ctx& c, int cnt, int ib, const float4* B, const int* act);
+// Slice A by rows into sa[ia], B by columns into sb[ib] (the most
+// significant `planes` slices); C = alpha A B (+ D) (+ I).
+rgf_status sliceA(const Ctx& c, int cnt, int ia, const float4* A, const int* act, int planes = kSlices);
+rgf_status sliceB(const Ctx& c, int cnt, int ib, const float4* B, const int* act, int planes = kSlices);
 rgf_status mm(const Ctx& c, int cnt, int ia, int ib, float alpha, const float4* D, int addI, float4* C,
               const int* act);
 // C = A B + D from the four most significant slices of each operand.

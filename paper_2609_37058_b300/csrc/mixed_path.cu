@@ -25,13 +25,16 @@ size_t sb_bytes(int cnt, int b, int Kp, int nsl = kSlices) {
 }
 }  // namespace
 
-// Slice A by rows into sa[ia], B by columns into sb[ib].
-rgf_status sliceA(const Ctx& c, int cnt, int ia, const float4* A, const int* act) {
-    return slice_rows(cnt, c.b, c.b, A, c.nn, c.m->sa[ia], c.m->Kp, act, c.st);
+// Slice A by rows into sa[ia], B by columns into sb[ib] (the first `planes` slices).
+rgf_status sliceA(const Ctx& c, int cnt, int ia, const float4* A, const int* act, int planes) {
+    return slice_rows(cnt, c.b, c.b, A, c.nn, c.m->sa[ia], c.m->Kp, act, c.st, planes);
 }
-rgf_status sliceB(const Ctx& c, int cnt, int ib, const float4* B, const int* act) {
-    return slice_cols(cnt, c.b, c.b, B, c.nn, c.m->sb[ib], c.m->Kp, act, c.st);
+rgf_status sliceB(const Ctx& c, int cnt, int ib, const float4* B, const int* act, int planes) {
+    return slice_cols(cnt, c.b, c.b, B, c.nn, c.m->sb[ib], c.m->Kp, act, c.st, planes);
 }
+
+// Slices that mm4 reads: four on the tcgen05 core, all six on the reference core.
+static int mm4_planes(const Ctx& c) { return c.m->core == 1 ? kSlices : 4; }
 // C = alpha * A B (+ D) (+ I) from already sliced operands.
 rgf_status mm(const Ctx& c, int cnt, int ia, int ib, float alpha, const float4* D, int addI, float4* C,
               const int* act) {
@@ -69,7 +72,7 @@ rgf_status mm4(const Ctx& c, int cnt, int ia, int ib, const float4* D, float4* C
     g.active = act;
     g.status = c.m->status;
     g.bn = c.m->bn;
-    g.nsl = c.m->core == 1 ? 0 : 4;
+    g.nsl = mm4_planes(c) == kSlices ? 0 : mm4_planes(c);
     return oz_gemm(g, c.m->core, c.st);
 }
 
@@ -277,8 +280,9 @@ rgf_status inv_mixed_steps(const Ctx& c, int cnt, int W, const float4* M, float4
                 RGF_TRY(mm(c, cnt, 1, 0, -1.0f, nullptr, 1, R, m->bad));
             }
         }
-        RGF_TRY(sliceA(c, cnt, 0, X, cur));
-        RGF_TRY(sliceB(c, cnt, 0, R, cur));
+        // Operands of the correction are sliced only as far as mm4 reads them.
+        RGF_TRY(sliceA(c, cnt, 0, X, cur, mm4_planes(c)));
+        RGF_TRY(sliceB(c, cnt, 0, R, cur, mm4_planes(c)));
         RGF_TRY(mm4(c, cnt, 0, 0, X, X, cur));  // X += X R (a correction: four slices suffice)
         std::swap(cur, nxt);
         // Entries reseeded in FP64 at step 1 always continue (their check saw

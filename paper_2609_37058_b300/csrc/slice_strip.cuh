@@ -9,7 +9,8 @@
 // complex-expanded; rows of Kp BF16):
 //   slice s, row 2c  : (Re, -Im) of B[j][c] at K positions (2j, 2j+1)
 //   slice s, row 2c+1: (Im,  Re)
-// Only c < n, j < k are written (the K padding is zeroed once by the owner).
+// Only c < n, j < k and the first `planes` slices are written (the K padding
+// is zeroed once by the owner).
 //
 // Traits supply the element type (16 bytes: float4 double-float or double2),
 // the magnitude used for the column exponent, the exponent rule and the
@@ -31,7 +32,7 @@ inline bool strip_fits(int k) { return strip_smem_bytes(k) <= (size_t)kStripMaxS
 template <class Tr>
 __global__ void __launch_bounds__(kStripCols * 32, Tr::kMinBlocks) k_slice_cols_strip(int k, int n, const typename Tr::T* __restrict__ B,
                                                                       long sB, __nv_bfloat16* __restrict__ out, int Kp,
-                                                                      const int* __restrict__ active) {
+                                                                      const int* __restrict__ active, int planes) {
     using T = typename Tr::T;
     using M = typename Tr::M;
     constexpr int NS = Tr::NS;
@@ -82,6 +83,7 @@ __global__ void __launch_bounds__(kStripCols * 32, Tr::kMinBlocks) k_slice_cols_
         Tr::split(v, e, sr, si);
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
+            if (s >= planes) break;
             __nv_bfloat16* base = out + (((long)bi * NS + s) * rows) * Kp;
             __nv_bfloat162 p0, p1;
             p0.x = __float2bfloat16_rn(sr[s]);
