@@ -97,6 +97,10 @@ struct OzGemmHP {
     double2* C; long sC;
     const int* active;
     int* status;
+    // Slices of each operand that take part: 7 (0 = 7), or 5 for products
+    // whose result is a small correction (15 pairs, all five groups exact;
+    // relative error ~k 2^-39 of row-max x column-max).
+    int nsl;
 };
 rgf_status oz_gemm_hp(const OzGemmHP& g, cudaStream_t st);
 // Seven-digit slicing of FP64 complex operands (layouts as slice_rows /

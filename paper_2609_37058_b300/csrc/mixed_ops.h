@@ -95,8 +95,9 @@ rgf_status mm4(const Ctx& c, int cnt, int ia, int ib, const float4* D, float4* C
 // Seven-slice (FP64-class) counterparts for FP64 matrices.
 rgf_status hsliceA(const Ctx& c, int cnt, int ia, const double2* A, const int* act);
 rgf_status hsliceB(const Ctx& c, int cnt, int ib, const double2* B, const int* act);
+// nsl: slices of each operand in the product (0 = all seven, 5 for corrections).
 rgf_status hmm(const Ctx& c, int cnt, int ia, int ib, float alpha, const double2* D, int addI, double2* C,
-               const int* act);
+               const int* act, int nsl = 0);
 
 // X = M^-1 (df) for cnt entries: FP32 seed, Newton-Schulz refinement with a
 // Sherman-Morrison-scaled first step, FP64 reseed of entries that do not

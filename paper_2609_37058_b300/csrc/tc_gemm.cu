@@ -780,6 +780,11 @@ rgf_status oz_gemm_tc(const OzGemm& g, cudaStream_t st) {
 rgf_status oz_gemm_hp(const OzGemmHP& g, cudaStream_t st) {
     TcArgs a{g.batch, g.m, g.n, g.k, g.As, g.Bs, g.Kp, g.alpha, g.D, g.sD, g.add_identity, g.C, g.sC, g.active,
              g.status, TC_WAIT_NS, 0};
+    if (g.nsl == 5) return launch_tc<5, 5, 80, true, 32, kSlicesHP>(a, st);
+    if (g.nsl != 0 && g.nsl != kSlicesHP) {
+        set_error("oz_gemm_hp: unsupported slice count %d", g.nsl);
+        return RGF_E_INVALID;
+    }
     if (tc_bk() == 16) return launch_tc<kSlicesHP, kGroupsHP, 80, true, 16>(a, st);
     return launch_tc<kSlicesHP, kGroupsHP, 80, true, 32>(a, st);
 }
