@@ -1,0 +1,158 @@
+"""Pins for the extended-precision (80-bit) oracle, each independent of its code.
+
+* mpmath at 40 significant digits: the surface Green's function satisfies its
+  fixed-point equation g = (a - alpha g beta)^-1 to the 80-bit unit roundoff,
+  and the transmission equals T computed from the dense inverse of the whole
+  (z S - H - Sigma_L (+) Sigma_R) matrix (mpmath's own matrix inverse) on tiny
+  random nonorthogonal devices;
+* the uniform nearest-neighbour chain's closed form at finite eta, evaluated
+  in mpmath (the root of t l^2 - (z - eps) l + t = 0 with |l| < 1);
+* the FP64 oracle where T is not tiny, to its own rounding (2e-11 relative);
+* the FP64 oracle's own rounding: at the b = 8 workload's worst energy the
+  FP64 oracle moves under an exact gauge change by about as much as it
+  differs from this oracle, while this oracle does not move.
+"""
+import mpmath as mp
+import numpy as np
+import pytest
+
+from oracle import rgf_ext as x
+from oracle import rgf_oracle as o
+from synth import chain_device, make_workload, random_device
+from tests.helpers import gauge_transform
+
+mp.mp.dps = 40
+
+
+def _mpm(a):
+    a = np.asarray(a)
+    return mp.matrix([[mp.mpc(complex(v)) for v in row] for row in a])
+
+
+def _dag(m):
+    return m.transpose_conj()
+
+
+def _lead_mp(lead, z, side):
+    """(a, alpha, beta, c_lower, c_upper) of M = z S - H for one lead, in mpmath."""
+    a = z * _mpm(lead.S00) - _mpm(lead.H00)
+    lower = z * _mpm(lead.S10) - _mpm(lead.H10)
+    upper = z * _dag(_mpm(lead.S10)) - _dag(_mpm(lead.H10))
+    cl = z * _mpm(lead.Sc) - _mpm(lead.Hc)
+    cu = z * _dag(_mpm(lead.Sc)) - _dag(_mpm(lead.Hc))
+    return (a, upper, lower, cl, cu) if side == "R" else (a, lower, upper, cl, cu)
+
+
+def _fro(m):
+    return mp.sqrt(sum(abs(m[i, j]) ** 2 for i in range(m.rows) for j in range(m.cols)))
+
+
+def _surface_mp(lead, side, E, eta):
+    """The 80-bit surface GF, as an mpmath matrix (hi + lo), and its fixed-point
+    residual ||g - (a - alpha g beta)^-1|| / ||g|| evaluated at 40 digits."""
+    hi, lo, it = x.surface_gf(lead, side, E, eta)
+    assert it > 0
+    g = _mpm(hi) + _mpm(lo)
+    z = mp.mpc(E, eta)
+    a, al, be, _, _ = _lead_mp(lead, z, side)
+    res = _fro(g - mp.inverse(a - al * g * be)) / _fro(g)
+    return g, res
+
+
+@pytest.mark.parametrize("b,N,seed", [(1, 3, 11), (2, 3, 12), (3, 2, 13)])
+@pytest.mark.parametrize("E", [-0.7, 0.35, 1.2])
+def test_against_mpmath_dense(b, N, seed, E):
+    eta = 1e-3
+    dev = random_device(N, b, seed)
+    z = mp.mpc(E, eta)
+    gL, resL = _surface_mp(dev.lead_L, "L", E, eta)
+    gR, resR = _surface_mp(dev.lead_R, "R", E, eta)
+    # conditioned residual: ~1e3 x the 80-bit unit roundoff here (FP64 gives ~1e-13)
+    assert resL < 2e-15 and resR < 2e-15
+    _, _, _, cLl, cLu = _lead_mp(dev.lead_L, z, "L")
+    _, _, _, cRl, cRu = _lead_mp(dev.lead_R, z, "R")
+    sL = cLl * gL * cLu
+    sR = cRu * gR * cRl
+    # Dense (N b) x (N b) matrix z S - H - Sigma_L (+) Sigma_R, inverted by mpmath.
+    n = N * b
+    M = mp.matrix(n, n)
+    for i in range(N):
+        Ai = z * _mpm(dev.S_diag[i]) - _mpm(dev.H_diag[i])
+        for r in range(b):
+            for c in range(b):
+                M[i * b + r, i * b + c] = Ai[r, c]
+    for i in range(1, N):
+        lo_ = z * _mpm(dev.S_lower[i - 1]) - _mpm(dev.H_lower[i - 1])
+        up_ = z * _dag(_mpm(dev.S_lower[i - 1])) - _dag(_mpm(dev.H_lower[i - 1]))
+        for r in range(b):
+            for c in range(b):
+                M[i * b + r, (i - 1) * b + c] = lo_[r, c]
+                M[(i - 1) * b + r, i * b + c] = up_[r, c]
+    for r in range(b):
+        for c in range(b):
+            M[r, c] -= sL[r, c]
+            M[(N - 1) * b + r, (N - 1) * b + c] -= sR[r, c]
+    Gfull = mp.inverse(M)
+    G = mp.matrix(b, b)
+    for r in range(b):
+        for c in range(b):
+            G[r, c] = Gfull[r, (N - 1) * b + c]
+    gam = lambda s: mp.mpc(0, 1) * (s - _dag(s))
+    T_mp = mp.re(sum((gam(sL) * G * gam(sR) * _dag(G))[j, j] for j in range(b)))
+    T_x = x.transmission(dev, [E], eta)[0]
+    assert abs(T_x - float(T_mp)) <= 4e-16 * max(float(T_mp), 1e-3)
+
+
+def _chain_T_mp(E, eta, N, eps=0.0, t=1.0):
+    z = mp.mpc(E, eta)
+    d = mp.sqrt((z - eps) ** 2 - 4 * t * t)
+    l1, l2 = ((z - eps) + d) / (2 * t), ((z - eps) - d) / (2 * t)
+    lam = l1 if abs(l1) < 1 else l2
+    gam = -2 * t * mp.im(lam)
+    G = lam ** (N - 1) / (t * (1 / lam - lam))
+    return gam * gam * abs(G) ** 2
+
+
+@pytest.mark.parametrize("eta", [1e-2, 1e-6])
+def test_chain_closed_form_mpmath(eta):
+    N = 64
+    dev = chain_device(N)
+    E = np.linspace(-2.9, 2.9, 30)  # E = 0 left out: bipartite chain, see the FP64 pins
+    T_x = x.transmission(dev, E, eta)
+    for e, t in zip(E, T_x):
+        T_cf = float(_chain_T_mp(e, eta, N))
+        assert abs(t - T_cf) <= 2e-15 * max(T_cf, 1e-300) + 1e-300, (e, t, T_cf)
+
+
+def test_against_fp64_oracle_well_conditioned():
+    """On the b = 8 workload, at every grid energy with T > 1e-3 (24 of 256:
+    the 64 disordered layers leave T tiny elsewhere) the two agree to 2e-11
+    relative, with a median below 1e-12: the FP64 oracle's rounding through
+    64 layers at eta = 1e-6, no more."""
+    dev, E, eta = make_workload("small_N64_b8")
+    idx = np.array([78, 79, 84, 93, 95, 97, 99, 106, 107, 108, 110, 114, 120, 121, 122, 125,
+                    134, 135, 149, 155, 158, 160, 169, 186])
+    T_o = o.transmission(dev, E[idx], eta)
+    T_x = x.transmission(dev, E[idx], eta)
+    assert np.all(T_o > 1e-3)
+    rel = np.abs(T_x - T_o) / T_o
+    assert rel.max() <= 2e-11
+    assert np.median(rel) <= 1e-12
+
+
+def test_fp64_oracle_rounding_at_worst_energy():
+    """At index 139 of the b = 8 grid (E = 0.2706, T = 4.7e-7) the FP64 oracle
+    differs from this oracle by 1.2e-8 of T, i.e. 5.7 times the FP64 bar
+    1e-9 * max(T, 1e-6).  A random block-unitary gauge (an exact symmetry of
+    T, applied in FP64, so it perturbs the inputs by ~1e-16) moves this oracle
+    by at most 1e-10 of T but the FP64 oracle by more than 1e-9 of T: the
+    FP64 oracle's difference is its own arithmetic rounding, not the data's
+    sensitivity."""
+    dev, E, eta = make_workload("small_N64_b8")
+    e = E[[139]]
+    gdev = gauge_transform(dev, np.random.default_rng(5))
+    T_x, T_xg = x.transmission(dev, e, eta)[0], x.transmission(gdev, e, eta)[0]
+    T_o, T_og = o.transmission(dev, e, eta)[0], o.transmission(gdev, e, eta)[0]
+    assert abs(T_x - T_xg) <= 1e-10 * T_x
+    assert abs(T_o - T_x) > 1e-9 * max(T_x, 1e-6)
+    assert abs(T_og - T_o) > 1e-9 * T_x
