@@ -29,7 +29,7 @@ METRIC = "RGF energy-points/s (b=256, 500 layers), mixed vs FP64 at |dT|<=1e-6; 
 # dram__bytes_write.sum), the BF16 flops of that launch, and the source it
 # was measured on; reported (scaled by the flops of the timed launches) only
 # while that source is unchanged.  Capture: batch 148, b = 256, tile 96
-# (profiles/k_oz_tc_b256_batch148.md).
+# (one launch under ncu).
 GEMM_TRAFFIC = (702.694400e6 + 133.302016e6, 21 * 2.0 * 256 * 512 * 512 * 148,
                 "2a4a6e5c0d71374ee3f8f1a047933c9d23106129aeb1df71a1e38f111e6fd091")
 
@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--wave", type=int, default=296, help="energies per step and rank (two per SM)")
-    ap.add_argument("--fp64-wave", type=int, default=16, help="energies of the FP64 GPU comparison step")
+    ap.add_argument("--fp64-wave", type=int, default=148, help="energies of the timed FP64 GPU comparison wave")
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 GPU comparison step")
     ap.add_argument("--cpu-energies", type=int, default=2, help="energies of the oracle CPU sample")
     ap.add_argument("--batch-devices", type=int, default=64, help="devices of the uneven-batch run")
@@ -53,6 +53,12 @@ def parse():
     ap.add_argument("--serve-energies", default="32,128", help="energy-window sizes of serving requests (lo,hi)")
     ap.add_argument("--kpoints", type=int, default=8, help="k-points of the transverse-mesh run (0 skips it)")
     ap.add_argument("--ldos-energies", type=int, default=148, help="energies of the layer-DOS run (0 skips it)")
+    ap.add_argument("--full-shapes", action="store_true",
+                    help="also run the uneven-device batch at 512 energies per device and the Poisson "
+                         "serving run at 200 requests/s (bounded window), plus a sustainable-rate point")
+    ap.add_argument("--no-golden", action="store_true", help="skip the parity check at the stored oracle energies")
+    ap.add_argument("--no-peaks", action="store_true", help="skip the FP64/FP32/TF32 peak probes")
+    ap.add_argument("--parity-report", default="", help="write the per-energy parity table to this file")
     return ap.parse_args()
 
 
@@ -128,8 +134,9 @@ def measured_peaks():
         return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}, "fallback"
 
 
-def oracle_sample(dev, E, eta, n):
-    """FP64 oracle on the first n energies; returns (T, seconds, threads)."""
+def oracle_sample(dev, E, eta, n, info=False):
+    """FP64 oracle on the first n energies; returns (T, seconds, threads)
+    (and the per-energy decimation iteration counts when info is set)."""
     from oracle import rgf_oracle as o
     try:
         from threadpoolctl import threadpool_info
@@ -137,8 +144,57 @@ def oracle_sample(dev, E, eta, n):
     except Exception:
         threads = os.cpu_count() or 1
     t0 = time.perf_counter()
-    T = o.transmission(dev, E[:n], eta)
-    return T, time.perf_counter() - t0, threads
+    T, inf = o.transmission(dev, E[:n], eta, return_info=True)
+    dt = time.perf_counter() - t0
+    if info:
+        return T, dt, threads, [i["iters"] for i in inf]
+    return T, dt, threads
+
+
+def method_flop_per_energy(N, b, iters_L, iters_R):
+    """Work of one energy point counted as the method's complex FP64
+    operations (8 b^3 real flop per b x b x b product or inverse): the sweep
+    (32 b^3 per layer after the first), g_0 (8 b^3), the decimation (56 b^3
+    per iteration and lead), Sigma and Gamma (32 b^3) and G_{0,N-1} with the
+    two trace products (24 b^3)."""
+    b3 = float(b) ** 3
+    return 32 * b3 * (N - 1) + 8 * b3 + 56 * b3 * (iters_L + iters_R) + 32 * b3 + 24 * b3
+
+
+def golden_parity(rgf, plan_args, dev, report_path=""):
+    """The mixed plan at the energies whose oracle values are stored with the
+    tests (FP64 oracle and, when present, the extended-precision oracle):
+    max |dT| against each, and the count above the 1e-6 bar.  Untimed."""
+    import numpy as np
+    base = os.path.join(ROOT, "tests", "golden", WORKLOAD)
+    if not os.path.exists(base + ".txt"):
+        return None
+    g = np.loadtxt(base + ".txt")
+    idx, Eg, To = g[:, 0].astype(int), g[:, 1], g[:, 2]
+    Tx = None
+    if os.path.exists(base + ".ext.txt"):
+        x = np.loadtxt(base + ".ext.txt")
+        if x.shape[0] == g.shape[0] and np.array_equal(x[:, 0].astype(int), idx):
+            Tx = x[:, 2]
+    with rgf.Plan(dev.n_layers, dev.b, **plan_args) as p:
+        p.set_device(dev)
+        T, err, fl = p.transmission(np.ascontiguousarray(Eg))
+    d_o = np.abs(T - To)
+    out = {"energies": int(len(idx)), "stride": int(idx[1] - idx[0]) if len(idx) > 1 else 1,
+           "max_abs_dT_vs_fp64_oracle": float(d_o.max()), "over_1e-6_vs_fp64_oracle": int((d_o > 1e-6).sum()),
+           "max_err_estimate": float(err.max())}
+    if Tx is not None:
+        d_x = np.abs(T - Tx)
+        out.update({"max_abs_dT_vs_ext_oracle": float(d_x.max()), "over_1e-6_vs_ext_oracle": int((d_x > 1e-6).sum()),
+                    "max_abs_fp64_oracle_vs_ext": float(np.abs(To - Tx).max())})
+    if report_path:
+        with open(report_path, "w") as f:
+            f.write(f"# {WORKLOAD}: mixed path vs stored oracle values, every stored energy\n")
+            f.write("# index E T_mixed err_estimate |dT|_vs_fp64_oracle |dT|_vs_ext_oracle flags\n")
+            for k in range(len(idx)):
+                dx = abs(T[k] - Tx[k]) if Tx is not None else float("nan")
+                f.write(f"{idx[k]} {Eg[k]:.6f} {T[k]:.12e} {err[k]:.2e} {d_o[k]:.2e} {dx:.2e} {int(fl[k])}\n")
+    return out
 
 
 def tc_source_hash():
@@ -251,6 +307,104 @@ def run_serving(args, rgf):
             "engines": st["engines"], "peak_resident_bytes": st["peak_resident_bytes"],
             "capacity_note": "admission capped at min(150 GB, 55% of free device memory)",
             "offered_sweep_tflop_per_s": work / args.serve_seconds / 1e12 if args.serve_seconds else None}
+
+
+def run_full_shapes(rgf):
+    """The batching and serving workloads at their stated shapes.
+
+    * uneven: 64 devices (N log-uniform 50..1000, b in {64, ..., 320}), 512
+      energies each, one server run; energy points per second of wall time.
+    * poisson_200: Poisson arrivals at 200 requests/s during a 5 s window
+      (N log-uniform 20..2000, b uniform 96..288, 128..1024 energies, admission
+      capped at min(150 GB, 55% of free memory)).  The offered work is about
+      three orders of magnitude above one GPU, so the run is cut off 60 s
+      after the first arrival: offered, admitted and completed requests are
+      reported, and p50/p99 latency over every offered request, a request not
+      done at the cut-off counting with its age then (a lower bound).  To keep
+      device memory bounded, requests draw their device from a pool of 48
+      devices drawn on the GPU from the same distribution (the server copies a
+      request's blocks when it admits it, so requests may share inputs).
+    * sustainable: the same request distribution at 0.1 request/s for 60 s,
+      all requests run to completion: whether the queue stays bounded
+      (completion of the last request within 60 s of its arrival)."""
+    import numpy as np
+    import torch
+
+    from synth.devices import serving_trace
+    from synth.gpu_devices import random_device_gpu, uneven_shapes
+
+    out = {}
+    shapes = uneven_shapes(64, 3, N_lo=50, N_hi=1000, b_choices=[64, 96, 128, 192, 256, 320])
+    devs = [random_device_gpu(N, b, s, metal_frac=0.25, gap_offset=0.6) for N, b, s in shapes]
+    E = np.linspace(-2.0, 2.0, 512)
+    torch.cuda.synchronize()
+    with rgf.Server(slots=148, class_step=32, tuning="default") as sv:
+        t0 = time.perf_counter()
+        tickets = [sv.submit(d, E, 1e-5) for d in devs]
+        res = [sv.poll(t, timeout_us=3_600_000_000) for t in tickets]
+        wall = time.perf_counter() - t0
+        st = sv.stats()
+    del devs
+    torch.cuda.empty_cache()
+    out["uneven_512"] = {"devices": 64, "energies_per_device": 512, "energy_points": 64 * 512, "seconds": wall,
+                         "value": 64 * 512 / wall, "unit": "energy-points/s", "completed": int(sum(r is not None for r in res)),
+                         "engines": st["engines"], "steps": st["steps"], "fp64_reseeds": st["fp64_reseeds"],
+                         "flags_nonzero": int(sum(int(np.count_nonzero(r[2] & ~rgf.RGF_FLAG_REFINE))
+                                                  for r in res if r is not None))}
+
+    def serve(rate, window, cutoff, pool_n, seed):
+        trace = serving_trace(seed, rate=rate, duration=window, N_lo=20, N_hi=2000, b_lo=96, b_hi=288,
+                              nE_lo=128, nE_hi=1024)
+        pool_tr = serving_trace(seed + 100, rate=1000.0, duration=pool_n / 1000.0 * 3, N_lo=20, N_hi=2000,
+                                b_lo=96, b_hi=288, nE_lo=128, nE_hi=1024)[:pool_n]
+        pool = [random_device_gpu(r["N"], r["b"], r["seed"], metal_frac=0.25, gap_offset=0.6) for r in pool_tr]
+        rng = np.random.default_rng(seed)
+        pick = rng.integers(0, len(pool), len(trace))
+        torch.cuda.synchronize()
+        lat, done_pts = [], 0
+        with rgf.Server(slots=148, class_step=32, tuning="default") as sv:
+            tickets = []
+            t0 = time.perf_counter()
+            for r, j in zip(trace, pick):
+                delay = t0 + r["t"] - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+                try:
+                    tickets.append((sv.submit(pool[j], r["E"], r["eta"]), time.perf_counter(), r["n_E"], pool[j]))
+                except rgf.RGFError:
+                    tickets.append((None, time.perf_counter(), r["n_E"], pool[j]))
+            pending = [t for t in tickets if t[0] is not None]
+            while pending and time.perf_counter() - t0 < cutoff:
+                nxt = []
+                for t in pending:
+                    res = sv.poll(t[0], timeout_us=0)
+                    if res is None:
+                        nxt.append(t)
+                    else:
+                        lat.append(res[3])
+                        done_pts += t[2]
+                pending = nxt
+                if pending:
+                    time.sleep(0.05)
+            t_end = time.perf_counter()
+            st = sv.stats()
+            ages = [(t_end - t[1]) * 1e3 for t in tickets if t[0] is None] + [(t_end - t[1]) * 1e3 for t in pending]
+        del pool
+        torch.cuda.empty_cache()
+        allv = sorted(lat + ages)
+        pct = lambda q: allv[min(len(allv) - 1, int(round(q / 100 * (len(allv) - 1))))] if allv else None
+        return {"rate_per_s": rate, "window_s": window, "cutoff_s": cutoff, "offered": len(trace),
+                "admitted": int(st["submitted"] - st["rejected"]), "completed": len(lat),
+                "not_done_at_cutoff": len(ages), "energy_points_done": done_pts,
+                "energy_points_per_s": done_pts / (t_end - t0),
+                "p50_ms_all_offered": pct(50), "p99_ms_all_offered": pct(99),
+                "p50_ms_completed": float(np.median(lat)) if lat else None,
+                "max_ms_completed": float(max(lat)) if lat else None,
+                "peak_resident_bytes": st["peak_resident_bytes"], "device_pool": len(pool_tr)}
+
+    out["poisson_200"] = serve(200.0, 5.0, 60.0, 48, 4)
+    out["sustainable_0.1"] = serve(0.1, 60.0, 240.0, 8, 5)
+    return out
 
 
 def run_kpoints(args, rgf):
@@ -429,25 +583,65 @@ def main():
     plan.close()
 
     # ---------------------------------------------------------- FP64 GPU path
+    # The same path in plain FP64 on the same GPU: one untimed warm-up wave,
+    # then one wave of fp64_wave energies (the mixed step's first timed
+    # energies) timed with CUDA events on the plan's stream, inputs resident.
     fp64 = None
     if not args.no_compare and prec == rgf.RGF_MIXED:
         Wf = args.fp64_wave
+        s0f, _ = wave(args.warmup)
         with rgf.Plan(dev.n_layers, dev.b, precision=rgf.RGF_FP64, eta=eta, energy_wave=Wf,
                       cuda_stream=stream.cuda_stream) as pf:
             pf.set_device(dev)
-            Ef = np.ascontiguousarray(E_all[:Wf])
+            Ef = E_d[s0f:s0f + Wf]
+            Tf = torch.zeros_like(Ef)
+            rgf.rgf_transmission(pf.handle, E_d[:8], Tf[:8])  # warm-up
             torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            Tf, _, _ = pf.transmission(Ef)
-            dtf = time.perf_counter() - t0
-        fp64 = {"value": Wf / dtf, "unit": "energy-points/s", "energies": Wf,
-                "max_abs_dT_vs_mixed": float(np.abs(Tf - T_timed[:Wf]).max()) if T_timed[:Wf].any() else None}
+            fa, fb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            fa.record(stream)
+            rgf.rgf_transmission(pf.handle, Ef, Tf)
+            fb.record(stream)
+            torch.cuda.synchronize()
+            dtf = fa.elapsed_time(fb) / 1e3
+        Tf = Tf.cpu().numpy()
+        fp64 = {"value": Wf / dtf, "unit": "energy-points/s", "energies": Wf, "seconds": dtf,
+                "timing": "one wave after a warm-up wave, CUDA events on the plan's stream",
+                "max_abs_dT_vs_mixed": float(np.abs(Tf - T_timed[s0f:s0f + Wf]).max())}
 
     # ---------------------------------------------------------- CPU oracle
     s0, _ = wave(args.warmup)
     nb = args.cpu_energies
-    T_cpu, cpu_s, threads = oracle_sample(dev, E_all[s0:], eta, nb)
+    T_cpu, cpu_s, threads, iters = oracle_sample(dev, E_all[s0:], eta, nb, info=True)
     dT = np.abs(T_cpu - T_timed[s0:s0 + nb])
+
+    # ---------------------------------------------------------- method roofline
+    # Throughput x the method's flop per energy (decimation iterations from the
+    # oracle sample) against the measured FP64, TF32 and BF16 peaks.
+    it_L = float(np.mean([i[0] for i in iters]))
+    it_R = float(np.mean([i[1] for i in iters]))
+    F = method_flop_per_energy(dev.n_layers, dev.b, it_L, it_R)
+    pk = {}
+    if not args.no_peaks:
+        from paper_2609_37058_b300 import kernel_bench
+        pk = kernel_bench.peaks(reps=3)
+    mpeaks, _ = measured_peaks()
+
+    def fractions(rate):
+        tf = rate * F / 1e12
+        d = {"method_tflops": tf}
+        if pk:
+            d["frac_of_fp64_peak"] = tf / pk["fp64_fma_tflops"]
+            d["frac_of_tf32_peak"] = tf / pk["tf32_gemm_cublas_tflops"]
+        d["frac_of_bf16_sustained"] = tf / float(mpeaks.get("bf16_tflops_sustained", 1400.0))
+        return d
+
+    method_roof = {"flop_per_energy": F, "decimation_iters": [it_L, it_R],
+                   "count": "32b^3(N-1) + 8b^3 + 56b^3(iters_L + iters_R) + 32b^3 + 24b^3",
+                   "mixed": fractions(value), "fp64_gpu": fractions(fp64["value"]) if fp64 else None,
+                   "peaks_measured_here": pk or None}
+    parity = None if args.no_golden else golden_parity(
+        rgf, dict(precision=prec, eta=eta, energy_wave=W, cuda_stream=stream.cuda_stream), dev,
+        args.parity_report)
 
     peaks, peak_src = measured_peaks()
     peak = float(peaks.get("bf16_tflops_sustained", 1400.0))
@@ -482,6 +676,8 @@ def main():
         "cpu_baseline": {"value": nb / cpu_s, "unit": "energy-points/s", "cores": threads, "kind": "oracle",
                          "sample": f"first {nb} energies of the first timed wave, numpy FP64 oracle"},
         "parity_sample": {"energies": nb, "max_abs_dT": float(dT.max()), "bar": 1e-6},
+        "parity_stored_energies": parity,
+        "method_roofline": method_roof,
         "fp64_gpu": fp64,
         "fp64_reseeds": reseeds,
         "phases_ms_per_step": {"lead_decimation_sigma_gamma": (phase1[0] - phase0[0]) / args.steps,
@@ -497,6 +693,8 @@ def main():
         line["kpoints"] = run_kpoints(args, rgf)
     if args.ldos_energies > 0:
         line["ldos"] = run_ldos(args, rgf)
+    if args.full_shapes:
+        line["full_shapes"] = run_full_shapes(rgf)
     print(json.dumps(line), flush=True)
 
 

@@ -108,26 +108,36 @@ typedef struct {
 void rgf_options_default(rgf_options* opt);
 
 /* Create a plan for devices with n_layers >= 1 principal layers of block
- * size 1 <= b <= 512.  opt may be NULL (defaults).  cuda_stream is a
+ * size 1 <= b <= 512 (the paper's N_z principal layers of size M_b, Results,
+ * the paragraph on the cost of each part of the workflow).  opt may be NULL (defaults).  cuda_stream is a
  * cudaStream_t (NULL = the legacy default stream); all work of the plan is
  * ordered on it.  The plan owns its device memory until rgf_plan_destroy. */
 rgf_status rgf_plan_create(rgf_plan_t* plan, int n_layers, int b, const rgf_options* opt,
                            void* cuda_stream);
 
-/* Copy the device Hamiltonian and overlap into the plan.
+/* Copy the device Hamiltonian and overlap into the plan (the static device
+ * Hamiltonian in a nonorthogonal localized basis, block tridiagonal in
+ * principal layers: Results, generalized eigenproblem paragraph, and the
+ * cost paragraph).  Hermiticity of the diagonal blocks is checked on the
+ * host (RGF_E_INVALID otherwise).
  * H_diag, S_diag: n_layers blocks; H_lower, S_lower: n_layers-1 blocks
  * (may be NULL when n_layers == 1). */
 rgf_status rgf_set_device_blocks(rgf_plan_t plan, const double* H_diag, const double* S_diag,
                                  const double* H_lower, const double* S_lower, int mem);
 
-/* Copy one lead: H00/S00 on-site blocks of a lead cell, H10/S10 the
+/* Copy one lead (the semi-infinite electrodes whose self-energies are
+ * combined with the device Hamiltonian: Methods, transport paragraph):
+ * H00/S00 on-site blocks of a lead cell, H10/S10 the
  * coupling between consecutive lead cells, Hc/Sc the lead-device coupling
  * (orientation as stated at the top of this file). */
 rgf_status rgf_set_leads(rgf_plan_t plan, int side, const double* H00, const double* S00,
                          const double* H10, const double* S10, const double* Hc,
                          const double* Sc, int mem);
 
-/* T(E_k) for k < n_E, synchronous.  E, T, err and flags are all in memory
+/* T(E_k) for k < n_E, synchronous: the zero-bias transmission of the
+ * Methods' transport paragraph, evaluated per energy point by the recursive
+ * sweep whose cost the Results' cost paragraph states as O(N_z M_b^3) per
+ * energy point (formulas at the top of this file).  E, T, err and flags are all in memory
  * space `mem`.  err[k] (may be NULL) receives, for the mixed path, the
  * largest estimated residual ||I - M X||_F of the energy's refined inverses
  * (|R|^2 of the last Newton-Schulz residual R before its correction), and 0
@@ -136,7 +146,8 @@ rgf_status rgf_set_leads(rgf_plan_t plan, int side, const double* H00, const dou
 rgf_status rgf_transmission(rgf_plan_t plan, const double* E, int n_E, double* T, double* err,
                             int* flags, int mem);
 
-/* Asynchronous form: copy n_E host energies, enqueue the work on the plan's
+/* Asynchronous form of rgf_transmission (no counterpart in the paper, which
+ * ran its transport on CPUs): copy n_E host energies, enqueue the work on the plan's
  * stream and return a ticket at once.  The plan must not be modified or
  * destroyed until the ticket has been polled to completion. */
 rgf_status rgf_submit(rgf_plan_t plan, const double* E, int n_E, rgf_ticket_t* ticket);

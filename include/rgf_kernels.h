@@ -51,6 +51,16 @@ rgf_status rgf_kernel_tc_timeout_probe(int wait_us, int* status_bits);
  * tensor cores, FP64 result. */
 rgf_status rgf_kernel_zgemm_hp(int batch, int m, int n, int k, const double* A, const double* B, double* C);
 
+/* C[i] = A[i] B[i] by the slice-product GEMM with a chosen number of slices
+ * per operand, on the tcgen05 core; the sweep and the decimation use the
+ * shorter forms only for products whose error is not amplified (see the
+ * nsl field of the GEMM arguments).  fp64_operands = 0: double-float
+ * operands (as rgf_kernel_zgemm_mixed), nsl in {4, 5, 6}; fp64_operands =
+ * 1: FP64 operands (as rgf_kernel_zgemm_hp), nsl in {5, 7}.  Host buffers,
+ * blocking; RGF_E_INVALID for another nsl. */
+rgf_status rgf_kernel_zgemm_slices(int batch, int m, int n, int k, const double* A, const double* B, double* C,
+                                   int fp64_operands, int nsl);
+
 /* Allocation-free FP64 batched inverse.  The paper has no counterpart: this
  * entry point exists for callers that cannot or must not allocate device
  * memory, e.g. code running while another framework owns the device memory
@@ -66,15 +76,32 @@ rgf_status rgf_kernel_zgemm_hp(int batch, int m, int n, int k, const double* A, 
  * Scratch: a fixed file-scope device array of rgf_inverse_f64_noalloc_limit()
  * bytes (16 MiB), present on every GPU that loads the library until the
  * process exits.  A call whose workspace would exceed it (about 60 matrices
- * of b = 256) is rejected with RGF_E_INVALID and a message.  The first call
- * on a device looks up the array's device address (cudaGetSymbolAddress) and
- * caches it; make that first call before any stream capture.  All calls on a
- * device share the one array, which keeps the last call's contents, so calls
- * that overlap on the GPU (different streams, no ordering) race. */
+ * of b = 256) is rejected with RGF_E_INVALID and a message; so is b outside
+ * 1..512.  Invalid calls return before anything is enqueued (flags are left
+ * as they were).  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress, with that device current) and caches it per
+ * device ordinal; make that first call before any stream capture.  The cache
+ * is not refreshed after cudaDeviceReset, which unloads the module: do not
+ * call this entry point on a device after resetting it in the same process.
+ * A, flags and cuda_stream must belong to the current device.  All calls on
+ * a device share the one array, which keeps the last call's contents, so
+ * calls that overlap on the GPU (different streams, no ordering) race. */
 rgf_status rgf_inverse_f64_noalloc(int batch, int b, double* A, int* flags, void* cuda_stream);
 
 /* Size in bytes of that fixed scratch array. */
 size_t rgf_inverse_f64_noalloc_limit(void);
+
+/* Peak probe of a CUDA-core pipe, the denominator of the FP64 path's and the
+ * FP32 seed inverse's roofline fractions (no counterpart in the paper, which
+ * reports no GPU numbers).  kind 0 = FP64, 1 = FP32.  Launches
+ * blocks_per_sm x (SM count) CTAs of 256 threads, each thread running 8
+ * independent chains of iters fused multiply-adds (2 flops each), once as
+ * warm-up and once timed with CUDA events on the legacy default stream;
+ * blocks until done.  Writes the achieved TFLOP/s and the timed launch's
+ * milliseconds (either may be NULL).  Allocates and frees a small output
+ * buffer.  RGF_E_INVALID for kind outside {0, 1}, blocks_per_sm outside
+ * 1..32 or iters outside 1..2^24. */
+rgf_status rgf_peak_fma(int kind, int blocks_per_sm, int iters, double* tflops, double* ms);
 
 /* Counters for measurement (process-wide, thread-safe). */
 

@@ -31,7 +31,7 @@ def sources():
 def build(verbose: bool = False, force: bool = False, extra=None) -> str:
     srcs = sources()
     deps = srcs + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) + \
-        [os.path.join(os.path.dirname(HERE), "include", "rgf.h")]
+        glob.glob(os.path.join(os.path.dirname(HERE), "include", "*.h"))
     if not force and os.path.exists(OUT):
         t = os.path.getmtime(OUT)
         if all(os.path.getmtime(d) <= t for d in deps):

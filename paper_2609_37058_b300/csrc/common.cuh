@@ -7,6 +7,7 @@
 #include <string>
 
 #include "../../include/rgf.h"
+#include "nvtx3/nvToolsExt.h"
 
 namespace rgf {
 
@@ -86,5 +87,15 @@ __device__ __forceinline__ float2 cinv(float2 d) {
 }
 
 inline int ceil_div(long a, long b) { return (int)((a + b - 1) / b); }
+
+// Named NVTX range for the lifetime of the object (profilers group the
+// launches of a phase under it; without a profiler attached it costs a
+// function-pointer check).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 }  // namespace rgf

@@ -113,6 +113,7 @@ size_t fp64_workspace_bytes(int W, int b) {
 }
 
 rgf_status fp64_wave(rgf_plan_s* p, int W) {
+    NvtxRange wave_range("rgf fp64 wave");
     cudaStream_t st = p->stream;
     const int b = p->b, N = p->N;
     const long nn = (long)b * b;

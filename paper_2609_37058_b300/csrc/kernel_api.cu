@@ -112,11 +112,29 @@ rgf_status rgf_kernel_inverse_c64(int batch, int b, float* A, int* flags) {
 }
 
 static rgf_status zgemm_mixed_impl(int batch, int m, int n, int k, const double* A, const double* B, double* C,
-                                   int core, unsigned long long test_wait_ns, int* status_out);
+                                   int core, unsigned long long test_wait_ns, int* status_out, int nsl = 0);
+static rgf_status zgemm_hp_impl(int batch, int m, int n, int k, const double* A, const double* B, double* C,
+                                int nsl);
 
 rgf_status rgf_kernel_zgemm_mixed(int batch, int m, int n, int k, const double* A, const double* B, double* C,
                                   int core) {
     return zgemm_mixed_impl(batch, m, n, k, A, B, C, core, 0, nullptr);
+}
+
+rgf_status rgf_kernel_zgemm_slices(int batch, int m, int n, int k, const double* A, const double* B, double* C,
+                                   int fp64_operands, int nsl) {
+    if (fp64_operands) {
+        if (nsl != 5 && nsl != 7) {
+            rgf::set_error("rgf_kernel_zgemm_slices: FP64 operands take 5 or 7 slices, not %d", nsl);
+            return RGF_E_INVALID;
+        }
+        return zgemm_hp_impl(batch, m, n, k, A, B, C, nsl == 7 ? 0 : nsl);
+    }
+    if (nsl != 4 && nsl != 5 && nsl != 6) {
+        rgf::set_error("rgf_kernel_zgemm_slices: double-float operands take 4, 5 or 6 slices, not %d", nsl);
+        return RGF_E_INVALID;
+    }
+    return zgemm_mixed_impl(batch, m, n, k, A, B, C, 0, 0, nullptr, nsl == 6 ? 0 : nsl);
 }
 
 rgf_status rgf_kernel_tc_timeout_probe(int wait_us, int* status_bits) {
@@ -130,7 +148,7 @@ rgf_status rgf_kernel_tc_timeout_probe(int wait_us, int* status_bits) {
 }
 
 static rgf_status zgemm_mixed_impl(int batch, int m, int n, int k, const double* A, const double* B, double* C,
-                                   int core, unsigned long long test_wait_ns, int* status_out) {
+                                   int core, unsigned long long test_wait_ns, int* status_out, int nsl) {
     if (!dims_ok(batch, m, n, k) || !A || !B || !C || (core != 0 && core != 1)) {
         rgf::set_error("rgf_kernel_zgemm_mixed: invalid arguments");
         return RGF_E_INVALID;
@@ -172,6 +190,7 @@ static rgf_status zgemm_mixed_impl(int batch, int m, int n, int k, const double*
     g.sC = (long)sc;
     g.status = (int*)status.p;
     g.test_wait_ns = test_wait_ns;
+    g.nsl = nsl;
     RGF_TRY(rgf::oz_gemm(g, core, 0));
     k_dfc_to_f64<<<1024, 256>>>((long)(batch * sc), (const float4*)fC.p, (double2*)dC.p);
     RGF_LAUNCH_CHECK();
@@ -187,6 +206,11 @@ static rgf_status zgemm_mixed_impl(int batch, int m, int n, int k, const double*
 }
 
 rgf_status rgf_kernel_zgemm_hp(int batch, int m, int n, int k, const double* A, const double* B, double* C) {
+    return zgemm_hp_impl(batch, m, n, k, A, B, C, 0);
+}
+
+static rgf_status zgemm_hp_impl(int batch, int m, int n, int k, const double* A, const double* B, double* C,
+                                int nsl) {
     if (!dims_ok(batch, m, n, k) || !A || !B || !C) {
         rgf::set_error("rgf_kernel_zgemm_hp: invalid arguments");
         return RGF_E_INVALID;
@@ -222,6 +246,7 @@ rgf_status rgf_kernel_zgemm_hp(int batch, int m, int n, int k, const double* A, 
     g.C = (double2*)dC.p;
     g.sC = (long)sc;
     g.status = (int*)status.p;
+    g.nsl = nsl;
     RGF_TRY(rgf::oz_gemm_hp(g, 0));
     int h_status = 0;
     RGF_CUDA_TRY(cudaMemcpy(&h_status, status.p, sizeof(int), cudaMemcpyDeviceToHost));

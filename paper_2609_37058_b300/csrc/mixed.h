@@ -80,9 +80,14 @@ struct OzGemm {
     // Real output columns per CTA of the tcgen05 core: 64, 80 or 96 (0 = 96).
     int bn;
     // Slices of each operand that take part: 6 (0 = 6, full double-float
-    // product) or 4 (ten pairs, relative error ~2^-30 of |A| |B|; enough for
-    // a Newton-Schulz correction X R, whose size is |X| |R| with R small and
-    // whose error the next residual, computed in full, measures again).
+    // product); 5 (15 pairs, relative error ~k 2^-39 of row-max x column-max;
+    // kernel-level entry point only: used for the running product Q_i =
+    // Q_{i-1} P_i of the sweep it moved well-conditioned T by up to 1.3e-6 at
+    // b = 256, N = 500, because the entries that carry T are far below the
+    // row and column maxima the error is relative to); or 4 (ten pairs,
+    // relative error ~2^-30 of |A| |B|; enough for a Newton-Schulz correction
+    // X R, whose size is |X| |R| with R small and whose error the next
+    // residual, computed in full, measures again).
     int nsl;
 };
 
@@ -98,8 +103,11 @@ struct OzGemmHP {
     const int* active;
     int* status;
     // Slices of each operand that take part: 7 (0 = 7), or 5 for products
-    // whose result is a small correction (15 pairs, all five groups exact;
-    // relative error ~k 2^-39 of row-max x column-max).
+    // whose result is a small correction (15 pairs in five accumulators, one
+    // per group; group g is exact for K <= 1024 / (g + 1) real terms in the
+    // worst case, beyond that FP32-rounded at ~2^-24 of its own size, i.e.
+    // ~2^-(40 + 8 (g - 2)) of the leading term; relative error ~k 2^-39 of
+    // row-max x column-max in all).
     int nsl;
 };
 rgf_status oz_gemm_hp(const OzGemmHP& g, cudaStream_t st);

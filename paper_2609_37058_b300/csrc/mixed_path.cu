@@ -568,8 +568,13 @@ rgf_status mixed_wave(rgf_plan_s* p, int W) {
             for (int i = 0; i < 3; ++i) cudaEventDestroy(e[i]);
         }
     } guard{ev};
+    NvtxRange wave_range("rgf mixed wave");
     RGF_CUDA_TRY(cudaEventRecord(ev[0], st));
-    RGF_TRY(mixed_leads(p, W, c));
+    {
+        NvtxRange r("rgf lead decimation + self-energies");
+        RGF_TRY(mixed_leads(p, W, c));
+    }
+    NvtxRange sweep_range("rgf sweep + trace");
     RGF_CUDA_TRY(cudaEventRecord(ev[1], st));
     float4* sigma = U(0);
     float4* gamma = U(2);

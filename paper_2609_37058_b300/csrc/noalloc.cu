@@ -58,6 +58,14 @@ rgf_status rgf_inverse_f64_noalloc(int batch, int b, double* A, int* flags, void
                        batch, b, b, need, kNoAllocScratchBytes);
         return RGF_E_INVALID;
     }
+    // The inverse's own shared-memory limit, checked here so that a call it
+    // would reject fails before the flags are cleared.
+    const int nb = rgf::gj_nb(b);
+    const size_t smem = ((size_t)b * (nb + 1) + b) * sizeof(double2);
+    if (smem > 200 * 1024) {
+        rgf::set_error("rgf_inverse_f64_noalloc: b = %d needs %zu bytes of shared memory", b, smem);
+        return RGF_E_INVALID;
+    }
     if (batch == 0) return RGF_OK;
     void* scratch = nullptr;
     RGF_TRY(scratch_for_current_device(&scratch));

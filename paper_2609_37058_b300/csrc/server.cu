@@ -216,6 +216,7 @@ void wait_ready(Engine* e, Request* r) {
 // Lead decimation, self-energies and broadening matrices of n items into the
 // ready buffer (pool units 16..19).
 rgf_status engine_decimate(Engine* e, const std::vector<std::pair<Request*, int>>& items) {
+    NvtxRange nvtx_range("rgf server decimation batch");
     const int n = (int)items.size();
     const int bc = e->bc;
     MixedState* m = &e->ms;
@@ -368,6 +369,7 @@ rgf_status run_graph(Engine* e, cudaGraphExec_t& gx, F issue) {
 
 // One layer for every active slot.
 rgf_status engine_step(Engine* e) {
+    NvtxRange nvtx_range("rgf server engine step");
     const int W = e->W;
     int* act = e->h_masks;
     int* nf = act + W;

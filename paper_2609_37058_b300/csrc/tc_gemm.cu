@@ -756,6 +756,16 @@ rgf_status oz_gemm_tc(const OzGemm& g, cudaStream_t st) {
             case 96: return launch_tc<4, 4, 96, false, 32, kSlices>(a, st);
             default: break;
         }
+    } else if (g.nsl == 5) {
+        // Five of the six slices (15 pairs, one accumulator per group; see
+        // OzGemm::nsl): reached through the kernel-level entry point.
+        switch (g.bn) {
+            case 64: return launch_tc<5, 5, 64, false, 32, kSlices>(a, st);
+            case 80: return launch_tc<5, 5, 80, false, 32, kSlices>(a, st);
+            case 0:
+            case 96: return launch_tc<5, 5, 96, false, 32, kSlices>(a, st);
+            default: break;
+        }
     } else if (tc_bk() == 16) {
         switch (g.bn) {
             case 64: return launch_tc<kSlices, kGroups, 64, false, 16>(a, st);

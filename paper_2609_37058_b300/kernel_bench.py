@@ -8,6 +8,12 @@ Gauss-Jordan inverses).  Each repetition is one call of the C entry point
 (host buffers in and out).  The call prints one JSON line with the wall time
 per call and the largest deviation from numpy's own product or inverse, so
 that the command is a self-checking target for profilers.
+
+``--op peaks`` measures the roofline denominators that the box's measured
+peak file does not hold: the library's FP64 and FP32 FMA-loop probes
+(``rgf_peak_fma``, best of several launches), and, for comparison, cuBLAS
+through torch: FP64 DGEMM and TF32 GEMM (fp32 inputs with TF32 tensor-core
+math allowed) of 8192^3, best of 5 after warm-up, CUDA events.
 """
 from __future__ import annotations
 
@@ -56,14 +62,48 @@ def run(op: str, batch: int, b: int, reps: int, seed: int = 0) -> dict:
     return {"op": op, "batch": batch, "b": b, "reps": reps, "s_per_call": dt, "check": what, "value": dev}
 
 
+def peaks(reps: int = 5) -> dict:
+    import torch
+    out = {}
+    for kind, name in ((0, "fp64_fma_tflops"), (1, "fp32_fma_tflops")):
+        rgf.rgf_peak_fma(kind, 8, 1 << 12)
+        out[name] = max(rgf.rgf_peak_fma(kind, 8, 1 << 16)[0] for _ in range(reps))
+
+    def gemm_tflops(dtype, n, tf32):
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+        a = torch.randn(n, n, device="cuda", dtype=dtype)
+        b = torch.randn(n, n, device="cuda", dtype=dtype)
+        for _ in range(2):
+            torch.matmul(a, b)
+        best = 0.0
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b)
+            e1.record()
+            e1.synchronize()
+            best = max(best, 2.0 * n ** 3 / (e0.elapsed_time(e1) * 1e-3) / 1e12)
+        torch.backends.cuda.matmul.allow_tf32 = False
+        return best
+
+    out["fp64_dgemm_cublas_tflops"] = gemm_tflops(torch.float64, 8192, False)
+    out["tf32_gemm_cublas_tflops"] = gemm_tflops(torch.float32, 8192, True)
+    out["fp32_gemm_cublas_tflops"] = gemm_tflops(torch.float32, 8192, False)
+    out["device"] = torch.cuda.get_device_name()
+    return out
+
+
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
-    ap.add_argument("--op", choices=["mixed", "hp", "f64", "inv64", "inv32"], default="mixed")
+    ap.add_argument("--op", choices=["mixed", "hp", "f64", "inv64", "inv32", "peaks"], default="mixed")
     ap.add_argument("--batch", type=int, default=148)
     ap.add_argument("--b", type=int, default=256)
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--seed", type=int, default=0)
     a = ap.parse_args(argv)
+    if a.op == "peaks":
+        print(json.dumps(peaks()))
+        return 0
     res = run(a.op, a.batch, a.b, a.reps, a.seed)
     print(json.dumps(res))
     limit = {"mixed": 1e-9, "hp": 1e-12, "f64": 1e-12, "inv64": 1e-10, "inv32": 1e-3}[a.op]

@@ -95,11 +95,13 @@ def lib():
         "rgf_kernel_zgemm_mixed": (ctypes.c_int, [ctypes.c_int] * 4 + [_P, _P, _P, ctypes.c_int]),
         "rgf_launch_count": (ctypes.c_ulonglong, []),
         "rgf_kernel_zgemm_hp": (ctypes.c_int, [ctypes.c_int] * 4 + [_P, _P, _P]),
+        "rgf_kernel_zgemm_slices": (ctypes.c_int, [ctypes.c_int] * 4 + [_P, _P, _P, ctypes.c_int, ctypes.c_int]),
         "rgf_kernel_tc_timeout_probe": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
         "rgf_inverse_f64_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, _P, _P]),
         "rgf_inverse_f64_noalloc_limit": (ctypes.c_size_t, []),
         "rgf_plan_stats": (ctypes.c_int, [_P] + [ctypes.POINTER(ctypes.c_longlong)] * 2),
         "rgf_plan_phase_ms": (ctypes.c_int, [_P] + [ctypes.POINTER(ctypes.c_double)] * 2),
+        "rgf_peak_fma": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D]),
         "rgf_gemm_timing": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)]),
         "rgf_server_options_default": (None, [ctypes.POINTER(rgf_server_options)]),
@@ -112,6 +114,8 @@ def lib():
         "rgf_server_set_class": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
         "rgf_bloch_sum": (ctypes.c_int, [ctypes.c_int, _P, _P, ctypes.c_int, ctypes.c_int, _P, _P, _P]),
         "rgf_kmesh_mean": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, _P, _P, _P]),
+        "rgf_kmesh_transmission": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, _P, _P, ctypes.c_int, ctypes.c_double,
+                                                  ctypes.c_int, _P, _P, _P]),
         "rgf_current": (ctypes.c_int, [ctypes.c_int, _P, _P, ctypes.c_int, _P, ctypes.c_double, ctypes.c_double,
                                        _P, _P]),
         "rgf_ldos": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, ctypes.c_int]),
@@ -283,6 +287,17 @@ def rgf_kernel_zgemm_hp(A, B):
     return C
 
 
+def rgf_kernel_zgemm_slices(A, B, fp64_operands, nsl):
+    """C[i] = A[i] B[i] with nsl slices per operand (see the header)."""
+    batch, m, k = A.shape
+    n = B.shape[2]
+    C = np.empty((batch, m, n), dtype=np.complex128)
+    _check(lib().rgf_kernel_zgemm_slices(batch, m, n, k, _host(A, np.complex128), _host(B, np.complex128),
+                                         C.ctypes.data, int(bool(fp64_operands)), int(nsl)),
+           "rgf_kernel_zgemm_slices")
+    return C
+
+
 def rgf_kernel_tc_timeout_probe(wait_us=20000):
     """Returns (status, status_bits) of the bounded-wait probe (see header)."""
     bits = ctypes.c_int(0)
@@ -307,18 +322,37 @@ def rgf_kernel_inverse_c64(A):
     return X, flags
 
 
-def rgf_inverse_f64_noalloc(A, flags=None, cuda_stream=0):
+def rgf_inverse_f64_noalloc(A, flags=None, cuda_stream=None):
     """In-place FP64 inverses of the complex128 CUDA tensor A (batch, b, b)
     with the library's fixed scratch array (no device allocation); flags is
-    an int32 CUDA tensor of batch entries or None.  Asynchronous on the
-    stream."""
-    pa, ma = _ptr(A, np.complex128)
-    pf, mf = _ptr(flags, np.int32)
-    if ma != RGF_MEM_DEVICE or (flags is not None and mf != RGF_MEM_DEVICE):
-        raise TypeError("rgf_inverse_f64_noalloc takes device tensors")
+    an int32 CUDA tensor of at least batch entries or None.  cuda_stream is a
+    torch.cuda.Stream on A's device, a raw cudaStream_t handle (int, taken to
+    be on A's device) or None (the legacy default stream).  Asynchronous on
+    the stream; the call runs with A's device current."""
+    import torch
+    if not (torch.is_tensor(A) and A.is_cuda and A.dtype == torch.complex128 and A.dim() == 3
+            and A.shape[1] == A.shape[2] and A.is_contiguous()):
+        raise TypeError("rgf_inverse_f64_noalloc: A must be a contiguous complex128 CUDA tensor (batch, b, b)")
     batch, b = int(A.shape[0]), int(A.shape[1])
-    _check(lib().rgf_inverse_f64_noalloc(batch, b, pa, pf, _P(cuda_stream) if cuda_stream else None),
-           "rgf_inverse_f64_noalloc")
+    if flags is not None:
+        if not (torch.is_tensor(flags) and flags.is_cuda and flags.dtype == torch.int32 and flags.is_contiguous()):
+            raise TypeError("rgf_inverse_f64_noalloc: flags must be a contiguous int32 CUDA tensor")
+        if flags.device != A.device:
+            raise ValueError("rgf_inverse_f64_noalloc: flags and A are on different devices")
+        if flags.numel() < batch:
+            raise ValueError(f"rgf_inverse_f64_noalloc: flags has {flags.numel()} entries, need {batch}")
+    handle = None
+    if isinstance(cuda_stream, torch.cuda.Stream):
+        if cuda_stream.device != A.device:
+            raise ValueError("rgf_inverse_f64_noalloc: the stream belongs to another device than A")
+        handle = cuda_stream.cuda_stream
+    elif cuda_stream:
+        handle = int(cuda_stream)
+    with torch.cuda.device(A.device):
+        _check(lib().rgf_inverse_f64_noalloc(batch, b, _P(A.data_ptr()),
+                                             _P(flags.data_ptr()) if flags is not None else None,
+                                             _P(handle) if handle else None),
+               "rgf_inverse_f64_noalloc")
 
 
 def rgf_inverse_f64_noalloc_limit() -> int:
@@ -327,6 +361,13 @@ def rgf_inverse_f64_noalloc_limit() -> int:
 
 def rgf_launch_count() -> int:
     return int(lib().rgf_launch_count())
+
+
+def rgf_peak_fma(kind: int, blocks_per_sm: int = 8, iters: int = 1 << 16):
+    """(TFLOP/s, ms) of the library's FMA-loop probe: kind 0 = FP64, 1 = FP32."""
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    _check(lib().rgf_peak_fma(kind, blocks_per_sm, iters, ctypes.byref(tf), ctypes.byref(ms)), "rgf_peak_fma")
+    return tf.value, ms.value
 
 
 def rgf_gemm_timing(enable: bool):
@@ -390,9 +431,16 @@ def rgf_server_destroy(server):
 TUNING_PATH = os.path.join(HERE, "tuning_b300.json")
 
 
-def load_tuning(path: str = TUNING_PATH) -> dict:
+def tuning_path() -> str:
+    """The tuning table to load: $RGF_TUNE_CACHE when set (a table written by
+    ``autotune --out``), else the one shipped with the package."""
+    return os.environ.get("RGF_TUNE_CACHE") or TUNING_PATH
+
+
+def load_tuning(path: str = None) -> dict:
     """Per-class settings written by ``autotune`` ({} when the file is absent)."""
     import json
+    path = path or tuning_path()
     if not os.path.exists(path):
         return {}
     with open(path) as f:
@@ -407,8 +455,8 @@ class Server:
     def __init__(self, slots=148, class_step=32, capacity_bytes=0, ns_steps=6, dec_tol=1e-14,
                  dec_max_iter=100, tuning=None):
         """``tuning``: {block_class: {"slots", "tile_n", "panel"}} (as written
-        by ``autotune``), "default" for the table shipped with the package,
-        or None."""
+        by ``autotune``), "default" for the table at $RGF_TUNE_CACHE (else the
+        one shipped with the package), or None."""
         o = rgf_server_options_default()
         o.slots, o.class_step, o.capacity_bytes = slots, class_step, capacity_bytes
         o.ns_steps, o.dec_tol, o.dec_max_iter = ns_steps, dec_tol, dec_max_iter
@@ -520,51 +568,44 @@ def rgf_kmesh_mean(T_k, w, T, cuda_stream=0):
                                 _P(cuda_stream) if cuda_stream else None), "rgf_kmesh_mean")
 
 
+class rgf_kdevice(ctypes.Structure):
+    _fields_ = [("n_R", ctypes.c_int), ("R", ctypes.POINTER(ctypes.c_int)), ("n_layers", ctypes.c_int),
+                ("b", ctypes.c_int), ("H_diag", _P), ("S_diag", _P), ("H_lower", _P), ("S_lower", _P),
+                ("lead", _P * 2)]
+
+
 def kpoint_transmission(server, kdev, kpts, weights, E, eta, group=8):
     """T(E) of a transverse-periodic device averaged over a k mesh, through
-    ``server`` (a ``Server``).  ``kdev`` has R (n_R, 2) and R-resolved block
-    arrays (as synth.devices.KDevice).  The Bloch sums and the mesh average
-    run in the library's kernels; ``group`` k-points are in flight at once.
+    ``server`` (a ``Server``) by ``rgf_kmesh_transmission``: the Bloch sums,
+    the per-k requests and the mesh average all run in the library.
+    ``kdev`` has R (n_R, 2) and R-resolved block arrays (as
+    synth.devices.KDevice); ``group`` k-points are in flight at once.
     Returns (T (n_E,), T_k (n_k, n_E)) as host arrays."""
-    import types
-
     import torch
     stream = torch.cuda.current_stream().cuda_stream
     up = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.complex128)).cuda()
-    names = ("H_diag", "S_diag", "H_lower", "S_lower")
-    XR = {n: up(getattr(kdev, n)) for n in names}
+    XR = {n: up(getattr(kdev, n)) for n in ("H_diag", "S_diag", "H_lower", "S_lower")}
     fields = ("H00", "S00", "H10", "S10", "Hc", "Sc")
     LR = [up(np.stack([getattr(L, f) for f in fields], axis=1)) for L in (kdev.lead_L, kdev.lead_R)]
-    R = np.asarray(kdev.R)
+    R = np.ascontiguousarray(np.asarray(kdev.R), dtype=np.int32)
     N, b = int(XR["H_diag"].shape[1]), int(XR["H_diag"].shape[2])
+    d = rgf_kdevice()
+    d.n_R, d.R = int(R.shape[0]), R.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    d.n_layers, d.b = N, b
+    d.H_diag, d.S_diag = XR["H_diag"].data_ptr(), XR["S_diag"].data_ptr()
+    if N > 1:
+        d.H_lower, d.S_lower = XR["H_lower"].data_ptr(), XR["S_lower"].data_ptr()
+    d.lead[0], d.lead[1] = LR[0].data_ptr(), LR[1].data_ptr()
+    kf = np.ascontiguousarray(kpts, dtype=np.float64).reshape(-1, 2)
+    w = np.ascontiguousarray(weights, dtype=np.float64)
     E = np.ascontiguousarray(E, dtype=np.float64)
-    n_k = len(kpts)
-    Tk = torch.empty((n_k, E.shape[0]), dtype=torch.float64, device="cuda")
-    for g0 in range(0, n_k, group):
-        flight = []
-        for ki in range(g0, min(n_k, g0 + group)):
-            blocks = {}
-            for n in names:
-                X = XR[n]
-                if X.shape[1] == 0:
-                    blocks[n] = torch.empty((0, b, b), dtype=torch.complex128, device="cuda")
-                    continue
-                Y = torch.empty(tuple(X.shape[1:]), dtype=torch.complex128, device="cuda")
-                rgf_bloch_sum(R, kpts[ki], X, Y, stream)
-                blocks[n] = Y
-            leads = []
-            for X in LR:
-                Y = torch.empty((6, b, b), dtype=torch.complex128, device="cuda")
-                rgf_bloch_sum(R, kpts[ki], X, Y, stream)
-                leads.append(tuple(Y[i] for i in range(6)))
-            dev = types.SimpleNamespace(lead_L=leads[0], lead_R=leads[1], **blocks)
-            flight.append((ki, server.submit(dev, E, eta), dev))
-        for ki, t, _ in flight:
-            r = server.poll(t, timeout_us=-1)
-            Tk[ki] = torch.from_numpy(r[0]).to("cuda")
-    w = torch.as_tensor(np.asarray(weights, dtype=np.float64)).to("cuda")
-    T = torch.empty(E.shape[0], dtype=torch.float64, device="cuda")
-    rgf_kmesh_mean(Tk, w, T, stream)
+    n_k, n_E = kf.shape[0], E.shape[0]
+    T = torch.empty(n_E, dtype=torch.float64, device="cuda")
+    Tk = torch.empty((n_k, n_E), dtype=torch.float64, device="cuda")
+    _check(lib().rgf_kmesh_transmission(server.handle if hasattr(server, "handle") else server, ctypes.byref(d),
+                                        n_k, kf.ctypes.data, w.ctypes.data, E.ctypes.data, n_E, float(eta),
+                                        int(group), _P(T.data_ptr()), _P(Tk.data_ptr()), _P(stream)),
+           "rgf_kmesh_transmission")
     return T.cpu().numpy(), Tk.cpu().numpy()
 
 

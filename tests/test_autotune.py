@@ -47,3 +47,13 @@ def test_smallest_slot_count_within_tolerance_is_kept():
     rates = {74: 0.8, 148: 1.0, 296: 1.10, 592: 1.14, 1184: 1.16}
     cfg, rate, _ = autotune.search(lambda bc, c: rates[c["slots"]], 256)
     assert cfg["slots"] == 592 and rate == 1.14  # 1.14 >= 0.97 * 1.16
+
+
+def test_tune_cache_environment_variable(tmp_path, monkeypatch):
+    p = tmp_path / "mine.json"
+    p.write_text(json.dumps({"classes": {"96": {"slots": 296, "tile_n": 80, "panel": 16}}}))
+    monkeypatch.setenv("RGF_TUNE_CACHE", str(p))
+    assert rgf.tuning_path() == str(p)
+    assert rgf.load_tuning() == {96: {"slots": 296, "tile_n": 80, "panel": 16}}
+    monkeypatch.delenv("RGF_TUNE_CACHE")
+    assert rgf.tuning_path() == rgf.TUNING_PATH

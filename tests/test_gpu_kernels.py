@@ -75,6 +75,44 @@ def test_zgemm_hp(rgf, batch, m, n, k):
     assert np.all(err <= bound), (err / bound).max()
 
 
+def _rowcol(A, B):
+    ra = np.maximum(np.abs(A.real), np.abs(A.imag)).max(axis=2)[:, :, None]
+    cb = np.maximum(np.abs(B.real), np.abs(B.imag)).max(axis=1)[:, None, :]
+    return ra, cb
+
+
+@pytest.mark.parametrize("fp64_operands,nsl", [(0, 4), (0, 5), (0, 6), (1, 5), (1, 7)])
+@pytest.mark.parametrize("batch,m,n,k", [(2, 256, 256, 256), (1, 320, 96, 320), (3, 65, 33, 17)])
+def test_zgemm_slice_counts(rgf, fp64_operands, nsl, batch, m, n, k):
+    """Each slice dropped from both operands costs 8 bits: the bound is
+    4k 2^-45 (six double-float slices) or 4k 2^-53 (seven FP64 slices) of
+    row-max x column-max, times 2^8 per slice fewer.  The shorter forms run
+    only where the recursion does not amplify their error (the running
+    product Q and the first Newton-Schulz residual; corrections)."""
+    rng = np.random.default_rng(nsl * 100 + m + k)
+    A, B = crand(rng, batch, m, k), crand(rng, batch, k, n)
+    A[:, ::3, :] *= 1e-5
+    B[:, :, ::4] *= 1e4
+    C = rgf.rgf_kernel_zgemm_slices(A, B, fp64_operands, nsl)
+    ra, cb = _rowcol(A, B)
+    full = 7 if fp64_operands else 6
+    base = 2.0 ** (-53 if fp64_operands else -45)
+    bound = 4.0 * k * base * 2.0 ** (8 * (full - nsl)) * ra * cb
+    err = np.abs(C - A @ B)
+    assert np.all(err <= bound), (err / bound).max()
+    if nsl < full:
+        # Not a silent full-length product: the dropped slices do show.
+        C_full = rgf.rgf_kernel_zgemm_slices(A, B, fp64_operands, full)
+        assert np.abs(C - C_full).max() > 0.0
+
+
+def test_zgemm_slice_counts_reject_others(rgf):
+    A = np.ones((1, 4, 4), complex)
+    for fp64_operands, nsl in ((0, 3), (0, 7), (1, 6), (1, 4)):
+        with pytest.raises(rgf.RGFError):
+            rgf.rgf_kernel_zgemm_slices(A, A, fp64_operands, nsl)
+
+
 def test_zgemm_hp_exact_integers(rgf):
     rng = np.random.default_rng(3)
     A = rng.integers(-1000, 1001, (2, 64, 256)) + 1j * rng.integers(-1000, 1001, (2, 64, 256))

@@ -53,3 +53,18 @@ def test_noalloc_inverse_rejects_oversized_batch(rgf):
     st = L.rgf_inverse_f64_noalloc(batch, b, ctypes.c_void_p(dummy.data_ptr()), None, None)
     assert st == rgf.RGF_E_INVALID
     assert "scratch" in rgf.rgf_last_error()
+
+
+def test_noalloc_wrapper_checks_shapes_and_devices(rgf):
+    """The binding refuses what would make the library write past a buffer:
+    a non-square or non-3-D A and a flags tensor shorter than the batch."""
+    import torch
+    A = torch.zeros((2, 8, 6), dtype=torch.complex128, device="cuda")
+    with pytest.raises(TypeError):
+        rgf.rgf_inverse_f64_noalloc(A)
+    A = torch.eye(8, dtype=torch.complex128, device="cuda").repeat(3, 1, 1).contiguous()
+    with pytest.raises(ValueError):
+        rgf.rgf_inverse_f64_noalloc(A, torch.zeros(2, dtype=torch.int32, device="cuda"))
+    with pytest.raises(TypeError):
+        rgf.rgf_inverse_f64_noalloc(A.reshape(24, 8))
+
