@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--serve-energies", default="32,128", help="energy-window sizes of serving requests (lo,hi)")
     ap.add_argument("--kpoints", type=int, default=8, help="k-points of the transverse-mesh run (0 skips it)")
     ap.add_argument("--ldos-energies", type=int, default=148, help="energies of the layer-DOS run (0 skips it)")
+    ap.add_argument("--kpm-moments", type=int, default=256, help="Chebyshev moments of the KPM run (0 skips it)")
+    ap.add_argument("--kpm-vectors", type=int, default=148, help="random vectors of the KPM run")
     ap.add_argument("--full-shapes", action="store_true",
                     help="also run the uneven-device batch at 512 energies per device and the Poisson "
                          "serving run at 200 requests/s (bounded window), plus a sustainable-rate point")
@@ -407,6 +409,41 @@ def run_full_shapes(rgf):
     return out
 
 
+def run_kpm(args, rgf):
+    """Non-orthogonal KPM Fermi level of the 200-layer b = 128 junction
+    (25,600 orbitals): power-iteration scale (100 steps), moments from
+    random-phase vectors (one CTA each), E_F at half filling.  FP64 on the
+    CUDA cores; the roofline is the FP64 pipe: 6 b x b block-vector products
+    per layer, step and vector (H v: 3, forward substitution: 1, backward:
+    2), 8 real flop per complex multiply-add."""
+    import numpy as np
+    import torch
+
+    from synth import make_workload
+    from synth.devices import random_phase_vectors
+
+    dev, _, _ = make_workload("junction_N200_b128")
+    N, b = dev.n_layers, dev.b
+    R = random_phase_vectors(args.kpm_vectors, N * b, seed=21)
+    x0 = random_phase_vectors(1, N * b, seed=22)[0]
+    M = args.kpm_moments
+    with rgf.KPM(dev) as k:
+        t0 = time.perf_counter()
+        alpha, beta = k.scale(x0, 100, 0.05)
+        t_scale = time.perf_counter() - t0
+        k.moments(R[:2], 4, alpha, beta)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mu = k.moments(R, M, alpha, beta)
+        t_mom = time.perf_counter() - t0
+        E_F = k.fermi_level(mu, alpha, beta, float(N * b))
+    flops = 8.0 * 6 * b * b * N * args.kpm_vectors * (M - 1)
+    return {"workload": "junction_N200_b128", "orbitals": N * b, "moments": M, "random_vectors": args.kpm_vectors,
+            "alpha": alpha, "E_F": E_F, "scale_seconds": t_scale, "moments_seconds": t_mom,
+            "fp64_tflops": flops / t_mom / 1e12,
+            "note": "one CTA per random vector, whole recursion in one launch; FP64 pipe bound"}
+
+
 def run_kpoints(args, rgf):
     """Transverse-periodic junction (R in {0, +1, -1}, 64 layers, b = 128)
     on an n x 1 Monkhorst-Pack mesh, 64 energies per k-point: Bloch sums,
@@ -693,6 +730,11 @@ def main():
         line["kpoints"] = run_kpoints(args, rgf)
     if args.ldos_energies > 0:
         line["ldos"] = run_ldos(args, rgf)
+    if args.kpm_moments > 0:
+        line["kpm"] = run_kpm(args, rgf)
+        if pk:
+            line["kpm"]["frac_of_fp64_peak"] = line["kpm"]["fp64_tflops"] / max(pk["fp64_fma_tflops"],
+                                                                                pk["fp64_dgemm_cublas_tflops"])
     if args.full_shapes:
         line["full_shapes"] = run_full_shapes(rgf)
     print(json.dumps(line), flush=True)

@@ -27,7 +27,11 @@ KPM (Weisse, Wellein, Alvermann, Fehske, Rev. Mod. Phys. 78, 275 (2006)):
   N(x) = g_0 mu_0 (pi - theta) / pi - (2 / pi) sum_{n>=1} g_n mu_n sin(n theta) / n
   (the integral of the kernel-damped Chebyshev density of states);
 * electron count spin * N(x); the Fermi level is the E where it equals the
-  target count, found by bisection on x in [-1, 1].
+  target count, found by bisection on x in [-1, 1];
+* the scale (a silent point of the paper): alpha from a power iteration on
+  S^-1 H from a given start vector (the largest |eps| from below) with a
+  safety margin, beta = 0.  For diagonally dominant overlaps a Gershgorin
+  bound also serves (used by the pins).
 
 Pins (tests/test_oracle_kpm.py): with the full unit-vector basis as random
 vectors the moments equal sum_i T_n(lambda_i) over the generalized
@@ -116,3 +120,17 @@ def gershgorin_scale(H, S, margin=0.01):
     if g <= 0:
         raise ValueError("overlap not diagonally dominant: no Gershgorin bound")
     return (1.0 + margin) * rho / g, 0.0
+
+
+def power_scale(H, S, x0, iters=100, margin=0.05):
+    """(alpha, beta): x <- S^-1 H x / |S^-1 H x| from x0, iters steps; the
+    last |S^-1 H x| for unit x estimates max |eps|; alpha = (1 + margin) of
+    it, beta = 0."""
+    x = np.asarray(x0, dtype=np.complex128).reshape(-1)
+    x = x / np.linalg.norm(x)
+    rho = 0.0
+    for _ in range(iters):
+        y = np.linalg.solve(S, H @ x)
+        rho = np.linalg.norm(y)
+        x = y / rho
+    return (1.0 + margin) * rho, 0.0

@@ -119,6 +119,14 @@ def lib():
         "rgf_current": (ctypes.c_int, [ctypes.c_int, _P, _P, ctypes.c_int, _P, ctypes.c_double, ctypes.c_double,
                                        _P, _P]),
         "rgf_ldos": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, ctypes.c_int]),
+        "rgf_kpm_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.c_int, _P, _P, _P, _P,
+                                          ctypes.c_int, _P]),
+        "rgf_kpm_scale": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_double, _D, _D]),
+        "rgf_kpm_moments": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_double, ctypes.c_int, _P, ctypes.c_int,
+                                           _P]),
+        "rgf_kpm_fermi": (ctypes.c_int, [ctypes.c_int, _P, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_double, _P, _P]),
+        "rgf_kpm_destroy": (ctypes.c_int, [_P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -684,6 +692,76 @@ class Plan:
     def close(self):
         if self.handle:
             rgf_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+# ----------------------------------------------------------------- KPM Fermi level (include/rgf_kpm.h)
+class KPM:
+    """Owns one rgf_kpm_t: the device's H and S on the GPU with S factored.
+    ``moments(R, n_mom, alpha, beta)`` takes the random vectors as a
+    (n_rand, N b) complex array (host or CUDA tensor) and returns mu as a
+    host array; ``fermi_level(mu, ...)`` runs the bisection kernel."""
+
+    def __init__(self, dev, cuda_stream=0):
+        import torch
+        self.N, self.b = int(dev.H_diag.shape[0]), int(dev.H_diag.shape[1])
+        self.stream = cuda_stream or torch.cuda.current_stream().cuda_stream
+        c = lambda a: np.ascontiguousarray(a, dtype=np.complex128)
+        arrs = [c(dev.H_diag), c(dev.S_diag)]
+        lows = [c(dev.H_lower), c(dev.S_lower)] if self.N > 1 else [None, None]
+        h = _P()
+        _check(lib().rgf_kpm_create(ctypes.byref(h), self.N, self.b, arrs[0].ctypes.data, arrs[1].ctypes.data,
+                                    lows[0].ctypes.data if lows[0] is not None else None,
+                                    lows[1].ctypes.data if lows[1] is not None else None, RGF_MEM_HOST,
+                                    _P(self.stream)), "rgf_kpm_create")
+        self.handle = h
+
+    def scale(self, x0, iters=100, margin=0.05):
+        """(alpha, beta) from a power iteration on S^-1 H started at x0."""
+        import torch
+        xd = torch.as_tensor(np.asarray(x0)).to(device="cuda", dtype=torch.complex128).contiguous()
+        if xd.numel() != self.N * self.b:
+            raise ValueError(f"x0 must have {self.N * self.b} entries")
+        a, b_ = ctypes.c_double(), ctypes.c_double()
+        _check(lib().rgf_kpm_scale(self.handle, _P(xd.data_ptr()), int(iters), float(margin), ctypes.byref(a),
+                                   ctypes.byref(b_)), "rgf_kpm_scale")
+        return a.value, b_.value
+
+    def moments(self, R, n_mom, alpha, beta):
+        import torch
+        Rd = torch.as_tensor(R).to(device="cuda", dtype=torch.complex128).contiguous()
+        if Rd.dim() != 2 or Rd.shape[1] != self.N * self.b:
+            raise ValueError(f"random vectors must be (n_rand, {self.N * self.b})")
+        mu = torch.empty(int(n_mom), dtype=torch.float64, device="cuda")
+        _check(lib().rgf_kpm_moments(self.handle, float(alpha), float(beta), int(Rd.shape[0]), _P(Rd.data_ptr()),
+                                     int(n_mom), _P(mu.data_ptr())), "rgf_kpm_moments")
+        return mu.cpu().numpy()
+
+    def fermi_level(self, mu, alpha, beta, n_electrons, spin=2.0):
+        import torch
+        mu_d = torch.as_tensor(np.ascontiguousarray(mu, dtype=np.float64)).cuda()
+        out = torch.empty(1, dtype=torch.float64, device="cuda")
+        _check(lib().rgf_kpm_fermi(int(mu_d.shape[0]), _P(mu_d.data_ptr()), float(alpha), float(beta),
+                                   float(n_electrons), float(spin), _P(out.data_ptr()), _P(self.stream)),
+               "rgf_kpm_fermi")
+        torch.cuda.synchronize()
+        return float(out.item())
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().rgf_kpm_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

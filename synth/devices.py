@@ -347,3 +347,11 @@ def monkhorst_pack(n1: int, n2: int = 1):
     k2 = (2.0 * np.arange(1, n2 + 1) - n2 - 1) / (2.0 * n2)
     k = np.array([[a, b_] for a in k1 for b_ in k2], dtype=np.float64)
     return k, np.full(k.shape[0], 1.0 / k.shape[0])
+
+
+def random_phase_vectors(n_vec: int, n: int, seed: int) -> np.ndarray:
+    """Random vectors for stochastic trace estimates: n_vec vectors of n
+    entries exp(2 pi i u), u uniform in [0, 1) (so E[r r^dag] = I and every
+    |r_j| = 1), numpy PCG64 seeded with ``seed``; shape (n_vec, n)."""
+    rng = np.random.default_rng(seed)
+    return np.exp(2j * np.pi * rng.random((n_vec, n)))

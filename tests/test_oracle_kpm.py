@@ -93,3 +93,18 @@ def test_jackson_kernel_values():
     g = kpm.jackson(64)
     assert abs(g[0] - 1.0) < 1e-15
     assert np.all(np.diff(g) < 0) and g[-1] > 0 and g[-1] < 1e-3
+
+
+@pytest.mark.parametrize("N,b,seed", [(4, 64, 5), (6, 64, 6)])
+def test_power_scale_covers_the_spectrum(N, b, seed):
+    """At b = 64 the synthetic overlap is not diagonally dominant (no
+    Gershgorin bound); 100 power steps on S^-1 H with a 5% margin still map
+    every generalized eigenvalue of scipy.linalg.eigh(H, S) into [-1, 1],
+    and not wastefully (alpha < 1.2 max |eps|)."""
+    dev, H, S, eps = _setup(N, b, seed)
+    with pytest.raises(ValueError):
+        kpm.gershgorin_scale(H, S)
+    x0 = np.exp(2j * np.pi * np.random.default_rng(seed).random(N * b))
+    alpha, beta = kpm.power_scale(H, S, x0, 100, 0.05)
+    assert beta == 0.0
+    assert np.abs(eps).max() < alpha < 1.2 * np.abs(eps).max()
