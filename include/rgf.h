@@ -90,6 +90,11 @@ typedef enum { RGF_LEAD_LEFT = 0, RGF_LEAD_RIGHT = 1 } rgf_side;
                                     first by the previous iteration's
                                     inverse), or the last Newton-Schulz step
                                     left ||I - M X||_F above 3e-7           */
+#define RGF_FLAG_LEAD_NEWTON 0x10 /* a lead's surface Green's function kept
+                                    its decimation value: the Newton step
+                                    that refines it diverged (its Stein
+                                    doubling grew instead of converging;
+                                    near band edges at small eta)          */
 
 typedef struct {
     int precision;     /* rgf_precision; default RGF_FP64 */

@@ -103,6 +103,18 @@ size_t rgf_inverse_f64_noalloc_limit(void);
  * 1..32 or iters outside 1..2^24. */
 rgf_status rgf_peak_fma(int kind, int blocks_per_sm, int iters, double* tflops, double* ms);
 
+/* Debug build (no counterpart in the paper).  librgf_debug.so is the same
+ * library compiled with -DRGF_DEBUG: the indices that kernels take from data
+ * (pivot rows of the Gauss-Jordan inverses, entries of the server's slot
+ * table) are checked on the device, and a failed check sets a bit
+ * (1: pivot row out of range, 2: slot-table entry out of range, 4: null
+ * block or result pointer of an active slot) instead of faulting; the kernel
+ * goes on with a safe index or skips the access.  rgf_debug_build() is 1 in
+ * that library and 0 in the normal one; rgf_debug_flags() returns the bits
+ * set since the last call and clears them (0 in the normal build). */
+int rgf_debug_build(void);
+unsigned rgf_debug_flags(void);
+
 /* Counters for measurement (process-wide, thread-safe). */
 
 /* Number of CUDA kernel launches issued by the library since load. */

@@ -17,7 +17,12 @@
  * with the device Hamiltonian).  The paper prints no RGF equation, so the steps
  * are the textbook ones:
  *   z = E + i eta multiplies S everywhere; M = z S - H;
- *   lead surface Green's function by Sancho-Rubio decimation of (a, alpha, beta);
+ *   lead surface Green's function: the retarded fixed point of
+ *   g = (a - alpha g beta)^-1, reached by Sancho-Rubio decimation of (a, alpha,
+ *   beta) and then, when the decimation converged, Newton steps on the
+ *   fixed-point equation (the decimation's recursion loses digits at some
+ *   energies: its result can leave a residual far above the rounding level,
+ *   which the Newton steps remove);
  *   Sigma_L = M_{0,-1} g_L M_{-1,0},  Sigma_R = M_{N-1,N} g_R M_{N,N-1};
  *   Gamma = i (Sigma - Sigma^dag);
  *   left-to-right sweep g_0 = (A_0 - Sigma_L)^-1, Q_0 = I,
@@ -25,6 +30,11 @@
  *     g_i = M_i^-1, Q_i = Q_{i-1} P_i, G_{0,N-1} = Q_{N-1} g_{N-1};
  *   T = Re Tr[Gamma_L G Gamma_R G^dag]  (the imaginary part is returned too).
  * Inverses are Gauss-Jordan elimination with partial pivoting on [M | I].
+ *
+ * Newton step for the fixed point: with r = (a - alpha g beta) g - I, the
+ * correction X solves the linearized (Stein) equation X = -g r + (g alpha) X
+ * (beta g), summed by doubling: X <- X + A X B, A <- A A, B <- B B, from
+ * X = -g r, A = g alpha, B = beta g, until |A|_F |B|_F <= tol; g <- g + X.
  *
  * Pins (tests/test_oracle_ext.py): mpmath dense inversion at 40 digits on tiny
  * random devices, with the surface Green's function checked by its fixed-point
@@ -183,6 +193,49 @@ static int sancho_rubio(cplx *gs, const cplx *a, cplx *alpha, cplx *beta, int b,
     return it <= max_iter ? it : -max_iter;
 }
 
+/* Newton steps on g = (a - alpha g beta)^-1 (see the header); alpha, beta are
+ * the lead's original couplings (not the decimated ones).  work: 9 bb.  A step
+ * whose doubling grows (|A|_F |B|_F above 1e4 times its first value, not
+ * finite, or not below tol after 200 doublings) is dropped and the function
+ * returns 0 with g as it was; a second step follows only when the first
+ * correction exceeded 1e-10 |g|_F.  Returns 1 when the refinement held. */
+static int newton_refine(cplx *g, const cplx *a, const cplx *alpha, const cplx *beta, int b, real tol,
+                         int steps, cplx *work) {
+    size_t bb = (size_t)b * b;
+    cplx *W = work, *r = work + bb, *A = work + 2 * bb, *B = work + 3 * bb, *X = work + 4 * bb,
+         *t1 = work + 5 * bb, *t2 = work + 6 * bb;
+    for (int s = 0; s < steps; ++s) {
+        gemm(t1, alpha, g, b);   /* alpha g */
+        gemm(t2, t1, beta, b);   /* alpha g beta */
+        for (size_t e = 0; e < bb; ++e) { W[e].re = a[e].re - t2[e].re; W[e].im = a[e].im - t2[e].im; }
+        gemm(r, W, g, b);        /* (a - alpha g beta) g */
+        for (int q = 0; q < b; ++q) r[(size_t)q * b + q].re -= 1.0L;
+        gemm(X, g, r, b);
+        for (size_t e = 0; e < bb; ++e) { X[e].re = -X[e].re; X[e].im = -X[e].im; }
+        gemm(A, g, alpha, b);
+        gemm(B, beta, g, b);
+        real p0 = -1.0L;
+        int converged = 0;
+        for (int k = 0; k < 200; ++k) {
+            gemm(t1, A, X, b);
+            gemm(t2, t1, B, b);
+            for (size_t e = 0; e < bb; ++e) { X[e].re += t2[e].re; X[e].im += t2[e].im; }
+            gemm(t1, A, A, b);
+            memcpy(A, t1, sizeof(cplx) * bb);
+            gemm(t1, B, B, b);
+            memcpy(B, t1, sizeof(cplx) * bb);
+            real p = fro(A, b) * fro(B, b);
+            if (p0 < 0.0L) p0 = p;
+            if (p <= tol) { converged = 1; break; }
+            if (!(p == p) || p > 1e4L * p0 || isinf(p)) break;
+        }
+        if (!converged) return 0;
+        for (size_t e = 0; e < bb; ++e) { g[e].re += X[e].re; g[e].im += X[e].im; }
+        if (fro(X, b) <= 1e-10L * fro(g, b)) break;
+    }
+    return 1;
+}
+
 /* Per-lead blocks of M = z S - H: on-site a, outward alpha, inward beta, and the
  * device-lead couplings c_lower (row right of column) and c_upper. */
 static void lead_blocks(const double *const *lead, cplx z, int b, int right, cplx *a, cplx *alpha,
@@ -204,25 +257,32 @@ static void lead_blocks(const double *const *lead, cplx z, int b, int right, cpl
  * iteration counts in it[0..1] (negative: not converged). */
 static void one_energy(int N, int b, const double *Hd, const double *Sd, const double *Hl,
                        const double *Sl, const double *const *leadL, const double *const *leadR,
-                       double E, double eta, real tol, int max_iter, double *T, double *Ti,
-                       int *it) {
+                       double E, double eta, real tol, int max_iter, int newton_steps, double *T,
+                       double *Ti, int *it) {
     size_t bb = (size_t)b * b;
     cplx z = { (real)E, (real)eta };
-    cplx *buf = (cplx *)calloc(bb * 26, sizeof(cplx));
+    cplx *buf = (cplx *)calloc(bb * 28, sizeof(cplx));
     cplx *a = buf, *al = buf + bb, *be = buf + 2 * bb, *cl = buf + 3 * bb, *cu = buf + 4 * bb;
     cplx *gL = buf + 5 * bb, *gR = buf + 6 * bb, *sL = buf + 7 * bb, *sR = buf + 8 * bb;
     cplx *t1 = buf + 9 * bb, *g = buf + 10 * bb, *Q = buf + 11 * bb, *P = buf + 12 * bb;
     cplx *M = buf + 13 * bb, *t2 = buf + 14 * bb, *work = buf + 15 * bb; /* 9 bb */
     cplx *gj = buf + 24 * bb;                                            /* 2 bb (b x 2b) */
+    cplx *al0 = buf + 26 * bb, *be0 = buf + 27 * bb;                     /* original couplings */
 
     /* Left lead: Sigma_L = M_{0,-1} g_L M_{-1,0} = c_lower g_L c_upper. */
     lead_blocks(leadL, z, b, 0, a, al, be, cl, cu);
+    memcpy(al0, al, sizeof(cplx) * bb);
+    memcpy(be0, be, sizeof(cplx) * bb);
     it[0] = sancho_rubio(gL, a, al, be, b, tol, max_iter, work);
+    if (newton_steps > 0 && it[0] > 0) newton_refine(gL, a, al0, be0, b, tol * tol, newton_steps, work);
     gemm(t1, cl, gL, b);
     gemm(sL, t1, cu, b);
     /* Right lead: Sigma_R = M_{N-1,N} g_R M_{N,N-1} = c_upper g_R c_lower. */
     lead_blocks(leadR, z, b, 1, a, al, be, cl, cu);
+    memcpy(al0, al, sizeof(cplx) * bb);
+    memcpy(be0, be, sizeof(cplx) * bb);
     it[1] = sancho_rubio(gR, a, al, be, b, tol, max_iter, work);
+    if (newton_steps > 0 && it[1] > 0) newton_refine(gR, a, al0, be0, b, tol * tol, newton_steps, work);
     gemm(t1, cu, gR, b);
     gemm(sR, t1, cl, b);
 
@@ -282,13 +342,13 @@ void rgf_ext_transmission(int N, int b, const double *H_diag, const double *S_di
                           const double *H_lower, const double *S_lower,
                           const double *const *lead_L, const double *const *lead_R,
                           const double *E, int n_E, double eta, double tol, int max_iter,
-                          double *T, double *T_imag, int *iters) {
+                          int newton_steps, double *T, double *T_imag, int *iters) {
 #pragma omp parallel for schedule(dynamic, 1)
     for (int k = 0; k < n_E; ++k) {
         double ti;
         int it[2];
         one_energy(N, b, H_diag, S_diag, H_lower, S_lower, lead_L, lead_R, E[k], eta,
-                   (real)tol, max_iter, &T[k], &ti, it);
+                   (real)tol, max_iter, newton_steps, &T[k], &ti, it);
         if (T_imag) T_imag[k] = ti;
         if (iters) { iters[2 * k] = it[0]; iters[2 * k + 1] = it[1]; }
     }
@@ -299,14 +359,17 @@ void rgf_ext_transmission(int N, int b, const double *H_diag, const double *S_di
  * and g_out_lo receives the rounding remainder (g80 - (double)g80) so that callers
  * can see the value to about 2^-64 of its magnitude. */
 int rgf_ext_surface_gf(int b, const double *const *lead, int side, double E, double eta,
-                       double tol, int max_iter, double *g_out, double *g_out_lo) {
+                       double tol, int max_iter, int newton_steps, double *g_out, double *g_out_lo) {
     size_t bb = (size_t)b * b;
     cplx z = { (real)E, (real)eta };
-    cplx *buf = (cplx *)calloc(bb * 16, sizeof(cplx));
+    cplx *buf = (cplx *)calloc(bb * 18, sizeof(cplx));
     cplx *a = buf, *al = buf + bb, *be = buf + 2 * bb, *cl = buf + 3 * bb, *cu = buf + 4 * bb;
-    cplx *gs = buf + 5 * bb, *work = buf + 6 * bb;
+    cplx *gs = buf + 5 * bb, *work = buf + 6 * bb, *al0 = buf + 16 * bb, *be0 = buf + 17 * bb;
     lead_blocks(lead, z, b, side, a, al, be, cl, cu);
+    memcpy(al0, al, sizeof(cplx) * bb);
+    memcpy(be0, be, sizeof(cplx) * bb);
     int it = sancho_rubio(gs, a, al, be, b, (real)tol, max_iter, work);
+    if (newton_steps > 0 && it > 0) newton_refine(gs, a, al0, be0, b, (real)tol * (real)tol, newton_steps, work);
     for (size_t e = 0; e < bb; ++e) {
         double hr = (double)gs[e].re, hi = (double)gs[e].im;
         g_out[2 * e] = hr; g_out[2 * e + 1] = hi;

@@ -6,8 +6,9 @@ CPU-baseline leg of ``bench.py`` may import this module.  The CUDA library
 never calls it and shares no code with it.
 
 ``transmission`` evaluates the same textbook steps as ``rgf_oracle`` (Sancho-
-Rubio leads, Sigma and Gamma, left-to-right sweep, Caroli trace) with every
-real number a 64-bit-significand ``long double``; energies run in parallel on
+Rubio leads refined by Newton steps on their fixed-point equation, Sigma and
+Gamma, left-to-right sweep, Caroli trace) with every real number a
+64-bit-significand ``long double``; energies run in parallel on
 the host cores.  It is pinned in ``tests/test_oracle_ext.py`` (mpmath dense
 inversion at 40 digits, the uniform-chain closed form in mpmath, the FP64
 oracle on well-conditioned energies).
@@ -45,11 +46,11 @@ def _load():
         lib.rgf_ext_transmission.argtypes = [
             ctypes.c_int, ctypes.c_int, dp, dp, dp, dp,
             ctypes.POINTER(dp), ctypes.POINTER(dp), dp, ctypes.c_int, ctypes.c_double,
-            ctypes.c_double, ctypes.c_int, dp, dp, ctypes.POINTER(ctypes.c_int)]
+            ctypes.c_double, ctypes.c_int, ctypes.c_int, dp, dp, ctypes.POINTER(ctypes.c_int)]
         lib.rgf_ext_transmission.restype = None
         lib.rgf_ext_surface_gf.argtypes = [
             ctypes.c_int, ctypes.POINTER(dp), ctypes.c_int, ctypes.c_double, ctypes.c_double,
-            ctypes.c_double, ctypes.c_int, dp, dp]
+            ctypes.c_double, ctypes.c_int, ctypes.c_int, dp, dp]
         lib.rgf_ext_surface_gf.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -69,12 +70,14 @@ def _lead_ptrs(lead, keep):
     return (ctypes.POINTER(ctypes.c_double) * 6)(*[_ptr(a) for a in arrs])
 
 
-def transmission(dev, energies, eta, tol=1e-18, max_iter=120, threads=None, return_info=False):
+def transmission(dev, energies, eta, tol=1e-18, max_iter=120, newton_steps=2, threads=None,
+                 return_info=False):
     """T(E) in extended precision, rounded to float64 at the end.
 
     ``tol`` is the Sancho-Rubio stop (max(||alpha||, ||beta||) <= tol ||a||);
     its default sits just above the long double unit roundoff, so the
-    decimation runs to the precision it carries.  ``threads`` sets
+    decimation runs to the precision it carries.  ``newton_steps`` Newton
+    steps on the fixed-point equation follow the decimation (0: none).  ``threads`` sets
     OMP_NUM_THREADS for this call's process if given before the first call.
     """
     if threads is not None:
@@ -92,14 +95,14 @@ def transmission(dev, energies, eta, tol=1e-18, max_iter=120, threads=None, retu
     Ti = np.empty(nE)
     it = np.empty(2 * nE, dtype=np.int32)
     lib.rgf_ext_transmission(N, b, _ptr(Hd), _ptr(Sd), _ptr(Hl), _ptr(Sl), pL, pR, _ptr(E), nE,
-                             float(eta), float(tol), int(max_iter), _ptr(T), _ptr(Ti),
+                             float(eta), float(tol), int(max_iter), int(newton_steps), _ptr(T), _ptr(Ti),
                              it.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
     if return_info:
         return T, dict(trace_imag=Ti, iters=it.reshape(nE, 2))
     return T
 
 
-def surface_gf(lead, side, E, eta, tol=1e-18, max_iter=120):
+def surface_gf(lead, side, E, eta, tol=1e-18, max_iter=120, newton_steps=2):
     """Surface Green's function of one lead (side 'L' or 'R') as (hi, lo)
     complex128 pairs: hi + lo is the 80-bit result to about 2^-64.  Returns
     (hi, lo, iterations); iterations < 0 means not converged."""
@@ -110,5 +113,5 @@ def surface_gf(lead, side, E, eta, tol=1e-18, max_iter=120):
     hi = np.empty((b, b), np.complex128)
     lo = np.empty((b, b), np.complex128)
     it = lib.rgf_ext_surface_gf(b, p, 1 if side == "R" else 0, float(E), float(eta), float(tol),
-                                int(max_iter), _ptr(hi), _ptr(lo))
+                                int(max_iter), int(newton_steps), _ptr(hi), _ptr(lo))
     return hi, lo, it

@@ -17,8 +17,14 @@ so the formulas are the textbook ones, in this notation:
   tau'_i = z S_{i-1,i} - H_{i-1,i} = z S_{i,i-1}^dag - H_{i,i-1}^dag.
 * Lead surface Green's functions g_s solve g_s = (a - alpha g_s beta)^-1,
   with a the lead on-site block of M, alpha the coupling from the surface
-  cell to the next cell away from the device, beta the coupling back; they
-  are found by Sancho-Rubio decimation.
+  cell to the next cell away from the device, beta the coupling back (the
+  retarded fixed point).  Sancho-Rubio decimation approaches it; at some
+  energies its recursion loses digits (the FP64 result can leave a fixed-
+  point residual of 1e-4 and a relative error of 1e-5), so Newton steps on
+  the fixed-point equation follow it: with r = (a - alpha g beta) g - I the
+  correction X solves the linearized (Stein) equation
+  X = -g r + (g alpha) X (beta g), summed by doubling (see newton_refine for
+  the rules that drop a step whose doubling grows instead of converging).
 * Sigma_L = tau_c^L g_L tau'_c^L sits on block (0,0); Sigma_R =
   tau'_c^R g_R tau_c^R sits on block (N-1,N-1); Gamma = i (Sigma - Sigma^dag).
 * G = (M - Sigma_L (+) Sigma_R)^-1, and T(E) = Re Tr[Gamma_L G_{0,N-1}
@@ -90,12 +96,64 @@ def sancho_rubio(a, alpha, beta, tol=1e-14, max_iter=100):
     return _inv(eps_s), max_iter, False
 
 
-def self_energies(dev, z, tol=1e-14, max_iter=100):
-    """Sigma_L, Sigma_R, Gamma_L, Gamma_R and the decimation iteration counts."""
+def newton_refine(a, alpha, beta, g, max_steps=2, tol=1e-28, max_doublings=100, growth=1e4,
+                  again=1e-8):
+    """Newton steps on g = (a - alpha g beta)^-1.  Returns (g, ok).
+
+    One step: r = (a - alpha g beta) g - I; the correction X solves the
+    linearized (Stein) equation X = -g r + A X B with A = g alpha, B = beta g,
+    summed by doubling (X <- X + A X B, A <- A A, B <- B B) until
+    p = |A|_F |B|_F <= tol; then g <- g + X.  The doubling converges when the
+    spectral radii of A and B multiply to less than one, as they do at the
+    retarded fixed point; a g far enough from it can break that (near band
+    edges at small eta), and the sums then grow: when p exceeds growth times
+    its first value, turns non-finite or has not reached tol after
+    max_doublings, the step is dropped, g is kept and ok is False.  A second
+    step follows only when the first correction exceeded again |g|_F (Newton
+    converges quadratically, so a smaller one leaves nothing to correct)."""
+    n = a.shape[0]
+    eye = np.eye(n, dtype=np.complex128)
+    for _ in range(max_steps):
+        r = (a - alpha @ g @ beta) @ g - eye
+        A = g @ alpha
+        B = beta @ g
+        X = -(g @ r)
+        p0 = None
+        converged = False
+        for _ in range(max_doublings):
+            X = X + A @ X @ B
+            A = A @ A
+            B = B @ B
+            p = np.linalg.norm(A) * np.linalg.norm(B)
+            if p0 is None:
+                p0 = p
+            if p <= tol:
+                converged = True
+                break
+            if not np.isfinite(p) or p > growth * p0:
+                break
+        if not converged:
+            return g, False
+        g = g + X
+        if np.linalg.norm(X) <= again * np.linalg.norm(g):
+            break
+    return g, True
+
+
+def self_energies(dev, z, tol=1e-14, max_iter=100, newton_steps=2):
+    """Sigma_L, Sigma_R, Gamma_L, Gamma_R, the decimation iteration counts and
+    whether each lead's Newton refinement held (refined = (left, right))."""
     aL, alL, beL, cLlow, cLup = lead_blocks(dev.lead_L, z, "L")
     aR, alR, beR, cRlow, cRup = lead_blocks(dev.lead_R, z, "R")
     gL, itL, okL = sancho_rubio(aL, alL, beL, tol, max_iter)
     gR, itR, okR = sancho_rubio(aR, alR, beR, tol, max_iter)
+    # Newton steps follow a converged decimation only (a truncated one is
+    # reported as such, and its result stays as it is).
+    refL = refR = False
+    if newton_steps > 0 and okL:
+        gL, refL = newton_refine(aL, alL, beL, gL, newton_steps)
+    if newton_steps > 0 and okR:
+        gR, refR = newton_refine(aR, alR, beR, gR, newton_steps)
     # Left: Sigma_L = M_{0,-1} g_L M_{-1,0}; M_{0,-1} is the lower block Lc.
     sig_L = cLlow @ gL @ cLup
     # Right: Sigma_R = M_{N-1,N} g_R M_{N,N-1}; M_{N-1,N} is the upper block.
@@ -103,7 +161,7 @@ def self_energies(dev, z, tol=1e-14, max_iter=100):
     gam_L = 1j * (sig_L - _dag(sig_L))
     gam_R = 1j * (sig_R - _dag(sig_R))
     return dict(sigma_L=sig_L, sigma_R=sig_R, gamma_L=gam_L, gamma_R=gam_R,
-                g_L=gL, g_R=gR, iters=(itL, itR), converged=(okL and okR))
+                g_L=gL, g_R=gR, iters=(itL, itR), converged=(okL and okR), refined=(refL, refR))
 
 
 def _A(dev, z, i):
@@ -201,7 +259,7 @@ def caroli(gamma_L, G1N, gamma_R):
 
 
 def transmission(dev, energies, eta, method="rgf", tol=1e-14, max_iter=100,
-                 return_info=False):
+                 return_info=False, newton_steps=2):
     """T(E) for each energy.  method: 'rgf' (left sweep), 'rgf_right'
     (mirror sweep) or 'dense' (full inversion)."""
     energies = np.asarray(energies, dtype=np.float64)
@@ -209,7 +267,7 @@ def transmission(dev, energies, eta, method="rgf", tol=1e-14, max_iter=100,
     info = []
     for k, E in enumerate(energies):
         z = complex(E, eta)
-        se = self_energies(dev, z, tol, max_iter)
+        se = self_energies(dev, z, tol, max_iter, newton_steps)
         if method == "rgf":
             G = rgf_G1N(dev, z, se["sigma_L"], se["sigma_R"])
         elif method == "rgf_right":
@@ -221,7 +279,8 @@ def transmission(dev, energies, eta, method="rgf", tol=1e-14, max_iter=100,
         t = caroli(se["gamma_L"], G, se["gamma_R"])
         T[k] = t.real
         if return_info:
-            info.append(dict(trace_imag=t.imag, iters=se["iters"], converged=se["converged"]))
+            info.append(dict(trace_imag=t.imag, iters=se["iters"], converged=se["converged"],
+                             refined=se["refined"]))
     return (T, info) if return_info else T
 
 

@@ -3,6 +3,8 @@
 ``python -m paper_2609_37058_b300.build`` (or ``build()``) compiles every
 ``csrc/*.cu`` with nvcc into ``paper_2609_37058_b300/librgf.so``.  The
 shared library is the product; the Python binding loads it with ctypes.
+``build(debug=True)`` (``-d``) compiles the same sources with -DRGF_DEBUG
+into ``librgf_debug.so`` (device-side index checks; see rgf_debug_flags).
 """
 from __future__ import annotations
 
@@ -14,6 +16,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "librgf.so")
+OUT_DEBUG = os.path.join(HERE, "librgf_debug.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -28,15 +31,17 @@ def sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
-def build(verbose: bool = False, force: bool = False, extra=None) -> str:
+def build(verbose: bool = False, force: bool = False, extra=None, debug: bool = False) -> str:
+    lib_out = OUT_DEBUG if debug else OUT
+    extra = list(extra or []) + (["-DRGF_DEBUG"] if debug else [])
     srcs = sources()
     deps = srcs + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) + \
         glob.glob(os.path.join(os.path.dirname(HERE), "include", "*.h"))
-    if not force and os.path.exists(OUT):
-        t = os.path.getmtime(OUT)
+    if not force and os.path.exists(lib_out):
+        t = os.path.getmtime(lib_out)
         if all(os.path.getmtime(d) <= t for d in deps):
-            return OUT
-    objdir = os.path.join(HERE, "_build")
+            return lib_out
+    objdir = os.path.join(HERE, "_build_debug" if debug else "_build")
     os.makedirs(objdir, exist_ok=True)
     objs = []
     procs = []
@@ -56,11 +61,11 @@ def build(verbose: bool = False, force: bool = False, extra=None) -> str:
             failed = True
     if failed:
         raise RuntimeError("nvcc failed")
-    cmd = [nvcc(), *ARCH, "-shared", "-o", OUT + ".tmp", *objs]
+    cmd = [nvcc(), *ARCH, "-shared", "-o", lib_out + ".tmp", *objs]
     subprocess.check_call(cmd)
-    os.replace(OUT + ".tmp", OUT)
-    return OUT
+    os.replace(lib_out + ".tmp", lib_out)
+    return lib_out
 
 
 if __name__ == "__main__":
-    print(build(verbose="-v" in sys.argv, force="-f" in sys.argv))
+    print(build(verbose="-v" in sys.argv, force="-f" in sys.argv, debug="-d" in sys.argv))

@@ -131,6 +131,11 @@ rgf_status rgf_plan_destroy(rgf_plan_t p) {
     cudaFree(p->d_dec_flags);
     cudaFree(p->d_active);
     cudaFree(p->d_iters);
+    cudaFree(p->d_nmask);
+    cudaFree(p->d_smask);
+    cudaFree(p->d_nnext);
+    cudaFree(p->d_status);
+    cudaFree(p->d_p0);
     cudaFree(p->d_remaining);
     cudaFree(p->d_anorm);
     if (p->h_remaining) cudaFreeHost(p->h_remaining);
@@ -216,6 +221,11 @@ rgf_status rgf_plan_create(rgf_plan_t* out, int n_layers, int b, const rgf_optio
     ALLOC(p->d_dec_flags, sizeof(int) * 2 * W);
     ALLOC(p->d_active, sizeof(int) * 2 * W);
     ALLOC(p->d_iters, sizeof(int) * 2 * W);
+    ALLOC(p->d_nmask, sizeof(int) * 2 * W);
+    ALLOC(p->d_smask, sizeof(int) * 2 * W);
+    ALLOC(p->d_nnext, sizeof(int) * 2 * W);
+    ALLOC(p->d_status, sizeof(int) * 2 * W);
+    ALLOC(p->d_p0, sizeof(double) * 2 * W);
     ALLOC(p->d_remaining, sizeof(int));
     ALLOC(p->d_anorm, sizeof(double) * 2 * W);
 #undef ALLOC

@@ -98,4 +98,33 @@ struct NvtxRange {
     NvtxRange& operator=(const NvtxRange&) = delete;
 };
 
+// ---------------------------------------------------------------- debug checks
+// The build with -DRGF_DEBUG checks on the device the indices that come from
+// data (pivot rows of the Gauss-Jordan inverses, entries of the server's
+// slot table).  A failed check ORs its bit into this translation unit's
+// device word and the kernel goes on with a safe index or skips the access:
+// no trap, no early exit before a barrier.  rgf_debug_flags() collects and
+// clears the words of every unit.  In the normal build RGF_DCHECK is true.
+enum : unsigned { RGF_DBG_PIVOT = 1u, RGF_DBG_SLOT = 2u, RGF_DBG_POINTER = 4u };
+void debug_register(unsigned (*collect)());
+#ifdef RGF_DEBUG
+static __device__ unsigned int g_debug_word;
+__device__ __forceinline__ bool debug_fail(unsigned bit) {
+    atomicOr(&g_debug_word, bit);
+    return false;
+}
+namespace {
+unsigned debug_collect_unit() {
+    unsigned h = 0, z = 0;
+    if (cudaMemcpyFromSymbol(&h, g_debug_word, sizeof(h)) != cudaSuccess) return 0x80000000u;
+    cudaMemcpyToSymbol(g_debug_word, &z, sizeof(z));
+    return h;
+}
+const int g_debug_unit_registered = (debug_register(&debug_collect_unit), 0);
+}  // namespace
+#define RGF_DCHECK(cond, bit) ((cond) || ::rgf::debug_fail(bit))
+#else
+#define RGF_DCHECK(cond, bit) true
+#endif
+
 }  // namespace rgf

@@ -55,6 +55,7 @@ __global__ void k_refill(int S, int bc, const SlotTab* __restrict__ tab, const i
     const int s = blockIdx.y;
     if (!refill[s]) return;
     const int r = tab[s].ready, D = tab[s].ready_D;
+    if (!RGF_DCHECK(r >= 0 && r < D, RGF_DBG_SLOT)) return;
     const long nn = (long)bc * bc;
     for (int k = 0; k < 4; ++k) {
         const float4* src = ready + ((long)k * D + r) * nn;
@@ -90,6 +91,7 @@ __global__ void k_form_step(int S, int bc, const SlotTab* __restrict__ tab, Slot
     if (!mk.act[s]) return;
     const SlotTab t = tab[s];
     const int nf = mk.nf ? mk.nf[s] : 0, fi = mk.first[s], la = mk.last[s];
+    if (!RGF_DCHECK(t.Sii && t.Hii && (!nf || (t.Sl && t.Hl)), RGF_DBG_POINTER)) return;
     const float2 zr = df_from_double(t.E), zi = df_from_double(t.eta);
     const long nn = (long)bc * bc, off = (long)s * nn;
     for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += (long)gridDim.x * blockDim.x) {
@@ -148,6 +150,7 @@ __global__ void k_finish(int S, const SlotTab* __restrict__ tab, const int* last
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= S || !last[s]) return;
     const SlotTab t = tab[s];
+    if (!RGF_DCHECK(t.outT && t.outErr && t.outFlags, RGF_DBG_POINTER)) return;
     *t.outT = slot_T[s];
     *t.outErr = slot_err[s];
     *t.outFlags = slot_flags[s];

@@ -270,4 +270,145 @@ rgf_status merge_dec_flags(int W, const int* dec_flags, const int* dec_active, i
     return RGF_OK;
 }
 
+// ------------------------------------------------------------- Newton refinement
+__global__ void k_newton_mask(int n, const int* mask, const int* dec_active, int* out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = ((mask ? mask[i] : 1) && !dec_active[i]) ? 1 : 0;
+}
+
+rgf_status newton_mask(int n, const int* mask, const int* dec_active, int* out, cudaStream_t st) {
+    if (n <= 0) return RGF_OK;
+    k_newton_mask<<<ceil_div(n, 128), 128, 0, st>>>(n, mask, dec_active, out);
+    RGF_LAUNCH_CHECK();
+    return RGF_OK;
+}
+
+__global__ void k_stein_check_f64(int b, const double2* A, const double2* B, double tol, double growth,
+                                  int first, double* p0, int* status, int* active, int* remaining) {
+    const int bi = blockIdx.x;
+    if (!active[bi]) return;
+    __shared__ double sh[32];
+    const long nn = (long)b * b, off = (long)bi * nn;
+    double sa = 0.0, sb = 0.0;
+    for (long i = threadIdx.x; i < nn; i += blockDim.x) {
+        sa += cabs2(A[off + i]);
+        sb += cabs2(B[off + i]);
+    }
+    const double ta = block_sum(sa, sh);
+    const double tb = block_sum(sb, sh);
+    if (threadIdx.x == 0) {
+        const double p = sqrt(ta) * sqrt(tb);
+        if (first) p0[bi] = p;
+        if (p <= tol) {
+            status[bi] = 1;
+            active[bi] = 0;
+        } else if (!isfinite(p) || p > growth * p0[bi]) {
+            status[bi] = 2;
+            active[bi] = 0;
+        } else {
+            atomicAdd(remaining, 1);
+        }
+    }
+}
+
+rgf_status stein_check_f64(int batch, int b, const double2* A, const double2* B, double tol, double growth,
+                           int first, double* p0, int* status, int* active, int* remaining, cudaStream_t st) {
+    if (batch <= 0) return RGF_OK;
+    k_stein_check_f64<<<batch, 256, 0, st>>>(b, A, B, tol, growth, first, p0, status, active, remaining);
+    RGF_LAUNCH_CHECK();
+    return RGF_OK;
+}
+
+__global__ void k_newton_finish_f64(int b, const double2* X, double2* g, const int* mask, const int* status,
+                                    double again, int* next, int* flags, int* remaining) {
+    const int bi = blockIdx.x;
+    if (!mask[bi]) {
+        if (threadIdx.x == 0) next[bi] = 0;
+        return;
+    }
+    __shared__ double sh[32];
+    const long nn = (long)b * b, off = (long)bi * nn;
+    const bool ok = status[bi] == 1;
+    double sx = 0.0, sg = 0.0;
+    for (long i = threadIdx.x; i < nn; i += blockDim.x) {
+        double2 v = g[off + i];
+        if (ok) {
+            const double2 x = X[off + i];
+            v.x += x.x;
+            v.y += x.y;
+            g[off + i] = v;
+            sx += cabs2(x);
+        }
+        sg += cabs2(v);
+    }
+    const double tx = block_sum(sx, sh);
+    const double tg = block_sum(sg, sh);
+    if (threadIdx.x == 0) {
+        const int more = ok && sqrt(tx) > again * sqrt(tg);
+        next[bi] = more;
+        if (more) atomicAdd(remaining, 1);
+        if (!ok) atomicOr(&flags[bi], RGF_FLAG_LEAD_NEWTON);
+    }
+}
+
+rgf_status newton_finish_f64(int batch, int b, const double2* X, double2* g, const int* mask, const int* status,
+                             double again, int* next, int* flags, int* remaining, cudaStream_t st) {
+    if (batch <= 0) return RGF_OK;
+    k_newton_finish_f64<<<batch, 256, 0, st>>>(b, X, g, mask, status, again, next, flags, remaining);
+    RGF_LAUNCH_CHECK();
+    return RGF_OK;
+}
+
+__global__ void k_sub_f64(int b, const double2* A, const double2* B, double2* C, const int* active) {
+    const int bi = blockIdx.y;
+    if (active && !active[bi]) return;
+    const long nn = (long)b * b, off = (long)bi * nn;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += (long)gridDim.x * blockDim.x)
+        C[off + i] = csub(A[off + i], B[off + i]);
+}
+
+rgf_status sub_f64(int batch, int b, const double2* A, const double2* B, double2* C, const int* active,
+                   cudaStream_t st) {
+    if (batch <= 0) return RGF_OK;
+    dim3 g(ceil_div((long)b * b, 256) < 16 ? ceil_div((long)b * b, 256) : 16, batch);
+    k_sub_f64<<<g, 256, 0, st>>>(b, A, B, C, active);
+    RGF_LAUNCH_CHECK();
+    return RGF_OK;
+}
+
+__global__ void k_axpy_masked_f64(int b, double alpha, const double2* X, double2* Y, const int* active) {
+    const int bi = blockIdx.y;
+    if (active && !active[bi]) return;
+    const long nn = (long)b * b, off = (long)bi * nn;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += (long)gridDim.x * blockDim.x) {
+        const double2 x = X[off + i];
+        double2 y = Y[off + i];
+        y.x = fma(alpha, x.x, y.x);
+        y.y = fma(alpha, x.y, y.y);
+        Y[off + i] = y;
+    }
+}
+
+rgf_status axpy_masked_f64(int batch, int b, double alpha, const double2* X, double2* Y, const int* active,
+                           cudaStream_t st) {
+    if (batch <= 0) return RGF_OK;
+    dim3 g(ceil_div((long)b * b, 256) < 16 ? ceil_div((long)b * b, 256) : 16, batch);
+    k_axpy_masked_f64<<<g, 256, 0, st>>>(b, alpha, X, Y, active);
+    RGF_LAUNCH_CHECK();
+    return RGF_OK;
+}
+
+__global__ void k_add_identity_f64(int b, double s, double2* A, const int* active) {
+    const int bi = blockIdx.x;
+    if (active && !active[bi]) return;
+    for (int r = threadIdx.x; r < b; r += blockDim.x) A[(long)bi * b * b + (long)r * b + r].x += s;
+}
+
+rgf_status add_identity_f64(int batch, int b, double s, double2* A, const int* active, cudaStream_t st) {
+    if (batch <= 0) return RGF_OK;
+    k_add_identity_f64<<<batch, 128, 0, st>>>(b, s, A, active);
+    RGF_LAUNCH_CHECK();
+    return RGF_OK;
+}
+
 }  // namespace rgf

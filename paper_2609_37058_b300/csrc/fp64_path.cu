@@ -103,6 +103,71 @@ rgf_status fp64_decimate(rgf_plan_s* p, int W, const int* mask, double2* pool_ba
     // g_s = eps_s^-1
     RGF_TRY(copy_f64(W2, b, g, eps_s, mask, st));
     RGF_TRY(inv_f64(W2, b, g, nn, inv_ws, nullptr, mask, st));
+
+    // Newton steps on the fixed-point equation g = (a - alpha g beta)^-1 for
+    // the converged entries: the decimation's recursion loses digits at some
+    // energies (relative errors up to ~1e-5 in FP64 with residuals up to
+    // ~1e-2); Newton takes g to the FP64 rounding level.  With
+    // r = (a - alpha g beta) g - I the correction X solves the Stein equation
+    // X = -g r + (g alpha) X (beta g), summed by doubling until
+    // |A|_F |B|_F <= dec_tol^2.  A doubling that grows instead (above 1e4
+    // times its first value: a g outside Newton's basin, near band edges at
+    // small eta) drops the step: g keeps its decimation value and the energy
+    // is flagged RGF_FLAG_LEAD_NEWTON.  A second step follows for the entries
+    // whose correction exceeded 1e-8 |g|_F.  a, alpha and beta are formed
+    // again (the decimation overwrote them).
+    {
+        double2 *a0 = pool.at(0), *al0 = pool.at(2), *be0 = pool.at(4), *Wm = pool.at(6), *r = pool.at(10);
+        double2 *A = pool.at(12), *B = pool.at(14), *X = pool.at(16), *u1 = pool.at(18), *u2 = pool.at(20);
+        int* nm = p->d_nmask;
+        int* nx = p->d_nnext;
+        int* sm = p->d_smask;
+        RGF_TRY(newton_mask(W2, mask, act, nm, st));
+        FormSrc a{{L[1], R[1]}, {L[0], R[0]}, {0, 0}};
+        FormSrc al{{L[3], R[3]}, {L[2], R[2]}, {0, 1}};
+        FormSrc be{{L[3], R[3]}, {L[2], R[2]}, {1, 0}};
+        RGF_TRY(form_f64(W, 2, b, E, eta, a, a0, nullptr, 0.0, nm, st));
+        RGF_TRY(form_f64(W, 2, b, E, eta, al, al0, nullptr, 0.0, nm, st));
+        RGF_TRY(form_f64(W, 2, b, E, eta, be, be0, nullptr, 0.0, nm, st));
+        const double stol = p->opt.dec_tol * p->opt.dec_tol;
+        for (int step = 0; step < 2; ++step) {
+            RGF_TRY(zgemm_f64(gemm_sq(W2, b, one, al0, g, u1, nm), st));   // alpha g
+            RGF_TRY(zgemm_f64(gemm_sq(W2, b, one, u1, be0, u2, nm), st));  // alpha g beta
+            RGF_TRY(sub_f64(W2, b, a0, u2, Wm, nm, st));
+            RGF_TRY(zgemm_f64(gemm_sq(W2, b, one, Wm, g, r, nm), st));
+            RGF_TRY(add_identity_f64(W2, b, -1.0, r, nm, st));              // r
+            RGF_TRY(zgemm_f64(gemm_sq(W2, b, mone, g, r, X, nm), st));      // X = -g r
+            RGF_TRY(zgemm_f64(gemm_sq(W2, b, one, g, al0, A, nm), st));
+            RGF_TRY(zgemm_f64(gemm_sq(W2, b, one, be0, g, B, nm), st));
+            RGF_CUDA_TRY(cudaMemcpyAsync(sm, nm, sizeof(int) * W2, cudaMemcpyDeviceToDevice, st));
+            RGF_CUDA_TRY(cudaMemsetAsync(p->d_status, 0, sizeof(int) * W2, st));
+            for (int k = 0; k < p->opt.dec_max_iter; ++k) {
+                RGF_TRY(zgemm_f64(gemm_sq(W2, b, one, A, X, u1, sm), st));  // A X
+                ZGemm acc = gemm_sq(W2, b, one, u1, B, X, sm);             // X + A X B
+                acc.beta = one;
+                acc.Cin = X;
+                acc.ldcin = b;
+                acc.sCin = nn;
+                RGF_TRY(zgemm_f64(acc, st));
+                RGF_TRY(zgemm_f64(gemm_sq(W2, b, one, A, A, u2, sm), st));
+                std::swap(A, u2);
+                RGF_TRY(zgemm_f64(gemm_sq(W2, b, one, B, B, u2, sm), st));
+                std::swap(B, u2);
+                RGF_CUDA_TRY(cudaMemsetAsync(p->d_remaining, 0, sizeof(int), st));
+                RGF_TRY(stein_check_f64(W2, b, A, B, stol, 1e4, k == 0, p->d_p0, p->d_status, sm, p->d_remaining,
+                                        st));
+                RGF_CUDA_TRY(cudaMemcpyAsync(p->h_remaining, p->d_remaining, sizeof(int), cudaMemcpyDeviceToHost, st));
+                RGF_CUDA_TRY(cudaStreamSynchronize(st));
+                if (*p->h_remaining == 0) break;
+            }
+            RGF_CUDA_TRY(cudaMemsetAsync(p->d_remaining, 0, sizeof(int), st));
+            RGF_TRY(newton_finish_f64(W2, b, X, g, nm, p->d_status, 1e-8, nx, p->d_dec_flags, p->d_remaining, st));
+            RGF_CUDA_TRY(cudaMemcpyAsync(p->h_remaining, p->d_remaining, sizeof(int), cudaMemcpyDeviceToHost, st));
+            RGF_CUDA_TRY(cudaStreamSynchronize(st));
+            if (*p->h_remaining == 0) break;
+            std::swap(nm, nx);
+        }
+    }
     *g_out = g;
     return RGF_OK;
 }

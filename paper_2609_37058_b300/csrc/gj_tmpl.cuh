@@ -278,6 +278,7 @@ __global__ void __launch_bounds__(256) k_gj_panel(int b, int k0, int nbk, T2* A,
 #pragma unroll
         for (int w = 1; w < NW; ++w) argmax_merge<R>(v, p, red_v[buf][w], red_i[buf][w]);
         if (p >= b) p = j;
+        if (!RGF_DCHECK(p >= j && p < b, RGF_DBG_PIVOT)) p = j;
         if (tid == 0) {
             pv[j] = p;
             if (!(v > 0) && flags) atomicOr(&flags[bi], RGF_FLAG_SINGULAR);
@@ -372,7 +373,8 @@ __global__ void __launch_bounds__(256) k_gj_swap(int b, int k0, int nbk, T2* A, 
         int n = nbk;
         for (int jj = 0; jj < nbk; ++jj) rows[jj] = k0 + jj;
         for (int jj = 0; jj < nbk; ++jj) {
-            const int p = pv[k0 + jj];
+            int p = pv[k0 + jj];
+            if (!RGF_DCHECK(p >= k0 + jj && p < b, RGF_DBG_PIVOT)) p = k0 + jj;
             int sp = -1;
             if (p < k0 + nbk) {
                 sp = p - k0;
@@ -429,7 +431,8 @@ __global__ void __launch_bounds__(256) k_gj_unpermute(int b, T2* A, long sA, con
     if (threadIdx.x == 0) {
         for (int c = 0; c < b; ++c) src[c] = c;
         for (int j = b - 1; j >= 0; --j) {
-            const int p = pv[j];
+            int p = pv[j];
+            if (!RGF_DCHECK(p >= j && p < b, RGF_DBG_PIVOT)) p = j;
             const int t = src[j];
             src[j] = src[p];
             src[p] = t;

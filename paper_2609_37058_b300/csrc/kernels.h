@@ -70,6 +70,31 @@ rgf_status copy_f64(int batch, int b, double2* dst, const double2* src, const in
 
 // Y[i] += alpha * X[i]  (real alpha)
 rgf_status axpy_f64(int batch, int b, double alpha, const double2* X, double2* Y, cudaStream_t st);
+// Newton refinement of the lead surface Green's functions (the retarded
+// fixed point of g = (a - alpha g beta)^-1; Sancho-Rubio's recursion loses
+// digits at some energies):
+// out[i] = (mask ? mask[i] : 1) && !dec_active[i]: the converged entries.
+rgf_status newton_mask(int n, const int* mask, const int* dec_active, int* out, cudaStream_t st);
+// Doubling of the Stein equation: for active i, p = |A_i|_F |B_i|_F (p0[i]
+// records p on the first call, first != 0); p <= tol: converged
+// (status[i] = 1, active[i] = 0); p not finite or > growth p0[i]: diverged
+// (status[i] = 2, active[i] = 0); else *remaining += 1 (zeroed by the caller).
+rgf_status stein_check_f64(int batch, int b, const double2* A, const double2* B, double tol, double growth,
+                           int first, double* p0, int* status, int* active, int* remaining, cudaStream_t st);
+// End of one Newton step for the entries of mask: converged (status 1):
+// g += X, and next[i] = |X|_F > again |g|_F (another step is worth taking);
+// otherwise g is kept, next[i] = 0 and flags[i] |= RGF_FLAG_LEAD_NEWTON.
+// Counts the next[] entries into *remaining (zeroed by the caller).
+rgf_status newton_finish_f64(int batch, int b, const double2* X, double2* g, const int* mask, const int* status,
+                             double again, int* next, int* flags, int* remaining, cudaStream_t st);
+// C[i] = A[i] - B[i] and Y[i] += alpha X[i] for active i (masks may be null).
+rgf_status sub_f64(int batch, int b, const double2* A, const double2* B, double2* C, const int* active,
+                   cudaStream_t st);
+rgf_status axpy_masked_f64(int batch, int b, double alpha, const double2* X, double2* Y, const int* active,
+                           cudaStream_t st);
+// A[i] += s I for active i.
+rgf_status add_identity_f64(int batch, int b, double s, double2* A, const int* active, cudaStream_t st);
+
 // flags[e] |= dec_flags[e] | dec_flags[W+e] | NOCONV bits from the
 // decimation active masks (still active after the last iteration).
 rgf_status merge_dec_flags(int W, const int* dec_flags, const int* dec_active, int* flags,

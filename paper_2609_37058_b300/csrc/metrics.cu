@@ -23,6 +23,19 @@ std::vector<Rec> g_recs;
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+namespace {
+std::mutex g_debug_mu;
+std::vector<unsigned (*)()>& debug_units() {
+    static std::vector<unsigned (*)()> v;
+    return v;
+}
+}  // namespace
+
+void debug_register(unsigned (*collect)()) {
+    std::lock_guard<std::mutex> lk(g_debug_mu);
+    debug_units().push_back(collect);
+}
+
 bool gemm_timing_enabled() { return g_timing.load(std::memory_order_relaxed); }
 
 void gemm_timing_before(cudaStream_t st, cudaEvent_t* a) {
@@ -43,6 +56,21 @@ void gemm_timing_after(cudaStream_t st, cudaEvent_t a, double flops) {
 extern "C" {
 
 unsigned long long rgf_launch_count(void) { return rgf::g_launches.load(); }
+
+int rgf_debug_build(void) {
+#ifdef RGF_DEBUG
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+unsigned rgf_debug_flags(void) {
+    std::lock_guard<std::mutex> lk(rgf::g_debug_mu);
+    unsigned w = 0;
+    for (auto f : rgf::debug_units()) w |= f();
+    return w;
+}
 
 rgf_status rgf_gemm_timing(int enable, double* total_ms, long long* launches, double* flops) {
     std::lock_guard<std::mutex> lk(rgf::g_mu);

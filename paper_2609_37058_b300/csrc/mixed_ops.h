@@ -8,7 +8,7 @@
 namespace rgf {
 
 constexpr int kPoolUnits = 20;  // df matrices, in units of W
-constexpr int kDecUnits = 26;   // FP64 decimation matrices, in units of W
+constexpr int kDecUnits = 32;   // FP64 decimation matrices, in units of W (26 + 6 kept for the Newton step)
 
 // Workspace of W energies of block size b, with lead decimation for Wd
 // energies (2 Wd lead entries) at a time.
@@ -43,6 +43,11 @@ struct MixedState {
     int* dec_flags = nullptr;
     double* dec_anorm = nullptr;
     int* dec_remaining = nullptr;
+    int* dec_newton = nullptr;  // 2Wd: converged entries (Newton-refined)
+    int* dec_smask = nullptr;   // 2Wd: the Newton step's doubling mask
+    int* dec_next = nullptr;    // 2Wd: entries that take a second Newton step
+    int* dec_status = nullptr;  // 2Wd: doubling outcome (1 converged, 2 diverged)
+    double* dec_p0 = nullptr;   // 2Wd: first doubling's |A| |B|
     int* h_remaining = nullptr;  // pinned
     int core = 0;                // 0 = tcgen05, 1 = mma.sync reference core
     int bn = 96;                 // tcgen05 tile width of the double-float GEMM (64, 80, 96)

@@ -167,7 +167,12 @@ rgf_status inv_hp(const Ctx& c, int cnt, int W, const double2* M, double2* X, do
 }
 
 // Sancho-Rubio decimation of the 2W lead entries formed in units 0, 2, 4, 6
-// of the decimation pool, with FP64 storage and seven-slice products.
+// of the decimation pool, with FP64 storage and seven-slice products, then
+// one Newton step on the fixed-point equation for the converged entries
+// (see hp_newton_step).
+rgf_status hp_newton_step(const Ctx& c, int W, double stol, int max_iter, const double2* a0, const double2* al0,
+                          const double2* be0, double2* g);
+
 rgf_status hp_decimate_run(const Ctx& c, int W, double tol, int max_iter, double2** g_out) {
     MixedState* m = c.m;
     cudaStream_t st = c.st;
@@ -175,6 +180,10 @@ rgf_status hp_decimate_run(const Ctx& c, int W, double tol, int max_iter, double
     auto U = [&](int unit) { return dec_unit(m, W, unit); };
     double2 *eps_s = U(0), *eps = U(2), *alpha = U(4), *beta = U(6), *g = U(8), *ga = U(10), *gb = U(12);
     double2 *t1 = U(14), *t2 = U(16), *t3 = U(18), *t4 = U(20), *R = U(22), *g_prev = U(24);
+    // The lead's own a, alpha, beta for the Newton step (the decimation overwrites them).
+    RGF_TRY(copy_f64(W2, b, U(26), eps_s, nullptr, st));
+    RGF_TRY(copy_f64(W2, b, U(28), alpha, nullptr, st));
+    RGF_TRY(copy_f64(W2, b, U(30), beta, nullptr, st));
     RGF_TRY(fro_norm_f64(W2, b, eps, m->dec_anorm, st));
     std::vector<int> ones(W2, 1);
     RGF_CUDA_TRY(cudaMemcpyAsync(m->dec_active, ones.data(), sizeof(int) * W2, cudaMemcpyHostToDevice, st));
@@ -213,7 +222,81 @@ rgf_status hp_decimate_run(const Ctx& c, int W, double tol, int max_iter, double
     RGF_TRY(merge_dec_flags(W, m->dec_flags, m->dec_active, c.flags, st));
     RGF_TRY(inv_hp(c, W2, W, eps_s, g, R, nullptr, m->dec_flags));
     RGF_TRY(merge_dec_flags(W, m->dec_flags, m->dec_active, c.flags, st));
+    RGF_TRY(hp_newton_step(c, W, tol * tol, max_iter, U(26), U(28), U(30), g));
+    RGF_TRY(merge_dec_flags(W, m->dec_flags, m->dec_active, c.flags, st));
     *g_out = g;
+    return RGF_OK;
+}
+
+// Newton steps on g = (a - alpha g beta)^-1 for the entries whose
+// decimation converged: Sancho-Rubio's recursion loses digits at some
+// energies (FP64-class results off by up to ~1e-5 relative, with fixed-point
+// residuals up to ~1e-2).  r = (a - alpha g beta) g - I from seven-slice
+// products (FP64-class, it is a small difference); the correction X solves
+// X = -g r + (g alpha) X (beta g), summed by doubling (X += A X B, A = A A,
+// B = B B) until |A|_F |B|_F <= stol, with five-slice products (X is a
+// correction); g += X.  A doubling that grows instead (above 1e4 times its
+// first value) drops the step: g keeps its decimation value and the entry is
+// flagged RGF_FLAG_LEAD_NEWTON.  A second step follows for the entries whose
+// correction exceeded 1e-8 |g|_F.  Uses decimation-pool units 0..7, 10..17.
+rgf_status hp_newton_step(const Ctx& c, int W, double stol, int max_iter, const double2* a0, const double2* al0,
+                          const double2* be0, double2* g) {
+    MixedState* m = c.m;
+    cudaStream_t st = c.st;
+    const int b = c.b, W2 = 2 * W;
+    auto U = [&](int unit) { return dec_unit(m, W, unit); };
+    double2 *Wm = U(0), *negr = U(2), *A = U(4), *B = U(6), *X = U(10), *u1 = U(12), *u2 = U(14), *u3 = U(16);
+    int* nm = m->dec_newton;
+    int* nx = m->dec_next;
+    int* sm = m->dec_smask;
+    RGF_TRY(newton_mask(W2, nullptr, m->dec_active, nm, st));
+    for (int step = 0; step < 2; ++step) {
+        RGF_TRY(hsliceA(c, W2, 0, al0, nm));
+        RGF_TRY(hsliceB(c, W2, 0, g, nm));
+        RGF_TRY(hmm(c, W2, 0, 0, 1.0f, nullptr, 0, u1, nm));           // alpha g
+        RGF_TRY(hsliceA(c, W2, 0, u1, nm));
+        RGF_TRY(hsliceB(c, W2, 1, be0, nm));
+        RGF_TRY(hmm(c, W2, 0, 1, 1.0f, nullptr, 0, u2, nm));           // alpha g beta
+        RGF_TRY(sub_f64(W2, b, a0, u2, Wm, nm, st));                     // a - alpha g beta
+        RGF_TRY(hsliceA(c, W2, 0, Wm, nm));
+        RGF_TRY(hmm(c, W2, 0, 0, -1.0f, nullptr, 1, negr, nm));        // I - (a - alpha g beta) g = -r
+        RGF_TRY(hsliceA(c, W2, 0, g, nm));
+        RGF_TRY(hsliceB(c, W2, 0, negr, nm));
+        RGF_TRY(hmm(c, W2, 0, 0, 1.0f, nullptr, 0, X, nm, 5));         // X = -g r
+        RGF_TRY(hsliceB(c, W2, 1, al0, nm));
+        RGF_TRY(hmm(c, W2, 0, 1, 1.0f, nullptr, 0, A, nm, 5));         // A = g alpha
+        RGF_TRY(hsliceA(c, W2, 0, be0, nm));
+        RGF_TRY(hsliceB(c, W2, 0, g, nm));
+        RGF_TRY(hmm(c, W2, 0, 0, 1.0f, nullptr, 0, B, nm, 5));         // B = beta g
+        RGF_CUDA_TRY(cudaMemcpyAsync(sm, nm, sizeof(int) * W2, cudaMemcpyDeviceToDevice, st));
+        RGF_CUDA_TRY(cudaMemsetAsync(m->dec_status, 0, sizeof(int) * W2, st));
+        for (int k = 0; k < max_iter; ++k) {
+            RGF_TRY(hsliceA(c, W2, 0, A, sm));
+            RGF_TRY(hsliceB(c, W2, 0, X, sm));
+            RGF_TRY(hmm(c, W2, 0, 0, 1.0f, nullptr, 0, u1, sm, 5));    // A X
+            RGF_TRY(hsliceA(c, W2, 1, u1, sm));
+            RGF_TRY(hsliceB(c, W2, 1, B, sm));
+            RGF_TRY(hmm(c, W2, 1, 1, 1.0f, X, 0, X, sm, 5));           // X + A X B
+            RGF_TRY(hsliceB(c, W2, 0, A, sm));
+            RGF_TRY(hmm(c, W2, 0, 0, 1.0f, nullptr, 0, u2, sm, 5));    // A A
+            RGF_TRY(hsliceA(c, W2, 1, B, sm));
+            RGF_TRY(hmm(c, W2, 1, 1, 1.0f, nullptr, 0, u3, sm, 5));    // B B
+            std::swap(A, u2);
+            std::swap(B, u3);
+            RGF_CUDA_TRY(cudaMemsetAsync(m->dec_remaining, 0, sizeof(int), st));
+            RGF_TRY(stein_check_f64(W2, b, A, B, stol, 1e4, k == 0, m->dec_p0, m->dec_status, sm, m->dec_remaining,
+                                    st));
+            RGF_CUDA_TRY(cudaMemcpyAsync(m->h_remaining, m->dec_remaining, sizeof(int), cudaMemcpyDeviceToHost, st));
+            RGF_CUDA_TRY(cudaStreamSynchronize(st));
+            if (*m->h_remaining == 0) break;
+        }
+        RGF_CUDA_TRY(cudaMemsetAsync(m->dec_remaining, 0, sizeof(int), st));
+        RGF_TRY(newton_finish_f64(W2, b, X, g, nm, m->dec_status, 1e-8, nx, m->dec_flags, m->dec_remaining, st));
+        RGF_CUDA_TRY(cudaMemcpyAsync(m->h_remaining, m->dec_remaining, sizeof(int), cudaMemcpyDeviceToHost, st));
+        RGF_CUDA_TRY(cudaStreamSynchronize(st));
+        if (*m->h_remaining == 0) break;
+        std::swap(nm, nx);
+    }
     return RGF_OK;
 }
 
@@ -313,7 +396,7 @@ size_t mixed_workspace_bytes(int W, int b) { return mixed_workspace_bytes(W, b, 
 size_t mixed_dec_bytes(int Wd, int b) {
     const int Kp = slice_pitch(b);
     return (size_t)kDecUnits * Wd * b * b * sizeof(double2) + 2 * sa_bytes(2 * Wd, b, Kp, kSlicesHP) +
-           2 * sb_bytes(2 * Wd, b, Kp, kSlicesHP) + (size_t)2 * Wd * (3 * sizeof(int) + sizeof(double)) + 4096;
+           2 * sb_bytes(2 * Wd, b, Kp, kSlicesHP) + (size_t)2 * Wd * (7 * sizeof(int) + 2 * sizeof(double)) + 4096;
 }
 
 rgf_status mixed_state_init(MixedState* m, int b, int W, void* ws, cudaStream_t st, int Wd, int slice_entries) {
@@ -405,6 +488,17 @@ rgf_status mixed_state_init(MixedState* m, int b, int W, void* ws, cudaStream_t 
         m->dec_flags = (int*)d;
         d += (size_t)2 * Wd * sizeof(int);
         m->dec_remaining = (int*)d;
+        d += 16;
+        m->dec_newton = (int*)d;
+        d += (size_t)2 * Wd * sizeof(int);
+        m->dec_smask = (int*)d;
+        d += (size_t)2 * Wd * sizeof(int);
+        m->dec_next = (int*)d;
+        d += (size_t)2 * Wd * sizeof(int);
+        m->dec_status = (int*)d;
+        d += (size_t)2 * Wd * sizeof(int);
+        d = (char*)(((uintptr_t)d + 15) & ~(uintptr_t)15);
+        m->dec_p0 = (double*)d;
         // The K padding of the slice buffers is never written: zero it once.
         RGF_CUDA_TRY(cudaMemsetAsync(m->hsa[0], 0,
                                      2 * sa_bytes(2 * Wd, b, m->Kp, kSlicesHP) + 2 * sb_bytes(2 * Wd, b, m->Kp, kSlicesHP),

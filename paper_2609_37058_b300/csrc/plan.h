@@ -39,6 +39,11 @@ struct rgf_plan_s {
     int* d_dec_flags = nullptr;  // 2W
     int* d_active = nullptr;     // 2W
     int* d_iters = nullptr;      // 2W
+    int* d_nmask = nullptr;      // 2W: entries refined by Newton steps, then the doubling's active mask
+    int* d_smask = nullptr;      // 2W
+    int* d_nnext = nullptr;      // 2W: entries that take a second Newton step
+    int* d_status = nullptr;     // 2W: doubling outcome (1 converged, 2 diverged)
+    double* d_p0 = nullptr;      // 2W: first doubling's |A| |B|
     int* d_remaining = nullptr;
     double* d_anorm = nullptr;   // 2W
     int* h_remaining = nullptr;  // pinned

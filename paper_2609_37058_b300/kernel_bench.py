@@ -9,6 +9,11 @@ Gauss-Jordan inverses).  Each repetition is one call of the C entry point
 per call and the largest deviation from numpy's own product or inverse, so
 that the command is a self-checking target for profilers.
 
+``--op kpm`` runs the KPM moments kernel on a seeded junction of
+``--layers`` layers of block size ``--b`` with ``--batch`` random-phase
+vectors and ``--moments`` moments (one launch); its self-check is that
+mu_0 equals the matrix size and no |mu_n| exceeds it.
+
 ``--op peaks`` measures the roofline denominators that the box's measured
 peak file does not hold: the library's FP64 and FP32 FMA-loop probes
 (``rgf_peak_fma``, best of several launches), and, for comparison, cuBLAS
@@ -62,6 +67,21 @@ def run(op: str, batch: int, b: int, reps: int, seed: int = 0) -> dict:
     return {"op": op, "batch": batch, "b": b, "reps": reps, "s_per_call": dt, "check": what, "value": dev}
 
 
+def kpm_run(layers: int, b: int, n_vec: int, n_mom: int, seed: int) -> dict:
+    from synth import random_device
+    from synth.devices import random_phase_vectors
+    dev = random_device(layers, b, seed, metal_frac=0.25, gap_offset=0.6)
+    n = layers * b
+    R = random_phase_vectors(n_vec, n, seed + 1)
+    with rgf.KPM(dev) as k:
+        alpha, beta = k.scale(random_phase_vectors(1, n, seed + 2)[0], 50, 0.1)
+        t0 = time.perf_counter()
+        mu = k.moments(R, n_mom, alpha, beta)
+        dt = time.perf_counter() - t0
+    return {"op": "kpm", "layers": layers, "b": b, "vectors": n_vec, "moments": n_mom, "s_per_call": dt,
+            "mu0_error": float(abs(mu[0] - n)), "max_abs_mu_over_mu0": float(np.abs(mu).max() / mu[0])}
+
+
 def peaks(reps: int = 5) -> dict:
     import torch
     out = {}
@@ -95,15 +115,21 @@ def peaks(reps: int = 5) -> dict:
 
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
-    ap.add_argument("--op", choices=["mixed", "hp", "f64", "inv64", "inv32", "peaks"], default="mixed")
+    ap.add_argument("--op", choices=["mixed", "hp", "f64", "inv64", "inv32", "peaks", "kpm"], default="mixed")
     ap.add_argument("--batch", type=int, default=148)
     ap.add_argument("--b", type=int, default=256)
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--layers", type=int, default=40, help="layers of the kpm op's junction")
+    ap.add_argument("--moments", type=int, default=16, help="moments of the kpm op")
     a = ap.parse_args(argv)
     if a.op == "peaks":
         print(json.dumps(peaks()))
         return 0
+    if a.op == "kpm":
+        res = kpm_run(a.layers, a.b, a.batch, a.moments, a.seed)
+        print(json.dumps(res))
+        return 0 if res["mu0_error"] == 0.0 and res["max_abs_mu_over_mu0"] <= 1.0 + 1e-9 else 1
     res = run(a.op, a.batch, a.b, a.reps, a.seed)
     print(json.dumps(res))
     limit = {"mixed": 1e-9, "hp": 1e-12, "f64": 1e-12, "inv64": 1e-10, "inv32": 1e-3}[a.op]

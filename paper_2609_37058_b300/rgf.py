@@ -14,7 +14,9 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "librgf.so")
+# RGF_DEBUG_LIB=1 in the environment loads the debug build (device-side
+# index checks, see rgf_debug_flags in include/rgf_kernels.h).
+LIB_PATH = os.path.join(HERE, "librgf_debug.so" if os.environ.get("RGF_DEBUG_LIB") == "1" else "librgf.so")
 
 RGF_OK, RGF_E_INVALID, RGF_E_OOM, RGF_E_CUDA, RGF_E_NOT_READY, RGF_E_NOCONV, RGF_E_TIMEOUT, \
     RGF_E_REJECTED, RGF_E_STATE = range(9)
@@ -94,6 +96,8 @@ def lib():
         "rgf_kernel_inverse_c64": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, _P]),
         "rgf_kernel_zgemm_mixed": (ctypes.c_int, [ctypes.c_int] * 4 + [_P, _P, _P, ctypes.c_int]),
         "rgf_launch_count": (ctypes.c_ulonglong, []),
+        "rgf_debug_build": (ctypes.c_int, []),
+        "rgf_debug_flags": (ctypes.c_uint, []),
         "rgf_kernel_zgemm_hp": (ctypes.c_int, [ctypes.c_int] * 4 + [_P, _P, _P]),
         "rgf_kernel_zgemm_slices": (ctypes.c_int, [ctypes.c_int] * 4 + [_P, _P, _P, ctypes.c_int, ctypes.c_int]),
         "rgf_kernel_tc_timeout_probe": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
@@ -494,7 +498,10 @@ class Server:
             E = torch.as_tensor(np.asarray(E, dtype=np.float64)).to("cuda")
             ptr = lambda t: t.data_ptr()
             n_E, mem = int(E.shape[0]), RGF_MEM_DEVICE
-            torch.cuda.synchronize()
+            # Wait for the producer of the arrays (torch's current stream)
+            # only: a device-wide synchronize is refused while an engine
+            # thread is capturing its step into a CUDA graph.
+            torch.cuda.current_stream(dev.H_diag.device).synchronize()
         else:
             c = lambda a: np.ascontiguousarray(a, dtype=np.complex128)
             arrs = {"H_diag": c(dev.H_diag), "S_diag": c(dev.S_diag)}

@@ -1,0 +1,72 @@
+"""Parity at every stored oracle energy (tests/golden), through the C ABI.
+
+Two references per workload, written by tests/golden/make_golden.py from
+oracle/ only:
+* <name>.txt       the FP64 oracle's T(E);
+* <name>.ext.txt   the extended-precision (80-bit) oracle's T(E).
+Both refine the lead surface Green's functions by Newton steps on their
+fixed-point equation, as the CUDA paths do (Sancho-Rubio alone leaves FP64
+errors up to ~1e-5 in g_s at some energies).  The FP64 oracle meets the FP64
+bar against the 80-bit values at every stored energy (tests/test_golden.py,
+no GPU), so both serve as references here.
+
+Bars, at every stored energy:
+* mixed path: |T - T_ext| <= 1e-6 and |T - T_fp64| <= 1e-6 (absolute);
+* FP64 path: |T - T_ext| <= 1e-9 max(T_ext, 1e-6).
+Every energy of the b = 8 and b = 128 grids; the 128 stored energies (every
+16th) of the b = 256 grid for the mixed path and 32 of them for the FP64
+path.  Flags other than an FP64 reseed (RGF_FLAG_REFINE) must be clear.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from helpers import FP64_REL, MIXED_ABS
+from synth import make_workload
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def golden(name):
+    g = np.loadtxt(os.path.join(HERE, "golden", f"{name}.txt"))
+    x = np.loadtxt(os.path.join(HERE, "golden", f"{name}.ext.txt"))
+    assert np.array_equal(g[:, 0], x[:, 0])
+    return g[:, 0].astype(int), g[:, 2], x[:, 2]
+
+
+@pytest.fixture(scope="module")
+def rgf():
+    from paper_2609_37058_b300 import build, rgf as r
+    build.build()
+    return r
+
+
+def run(rgf, name, idx, precision):
+    dev, E, eta = make_workload(name)
+    with rgf.Plan(dev.n_layers, dev.b, precision=precision, eta=eta) as p:
+        p.set_device(dev)
+        return p.transmission(E[idx])
+
+
+@pytest.mark.parametrize("name", ["small_N64_b8", "junction_N200_b128", "doped_N500_b256"])
+def test_mixed_every_stored_energy(rgf, name):
+    idx, T_o, T_x = golden(name)
+    T, err, flags = run(rgf, name, idx, rgf.RGF_MIXED)
+    assert np.all((flags & ~rgf.RGF_FLAG_REFINE) == 0), idx[(flags & ~rgf.RGF_FLAG_REFINE) != 0]
+    d_x, d_o = np.abs(T - T_x), np.abs(T - T_o)
+    assert d_x.max() <= MIXED_ABS, (idx[np.argmax(d_x)], d_x.max())
+    assert d_o.max() <= MIXED_ABS, (idx[np.argmax(d_o)], d_o.max())
+
+
+@pytest.mark.parametrize("name,stride", [("small_N64_b8", 1), ("junction_N200_b128", 1), ("doped_N500_b256", 4)])
+def test_fp64_stored_energies(rgf, name, stride):
+    idx, T_o, T_x = golden(name)
+    idx, T_o, T_x = idx[::stride], T_o[::stride], T_x[::stride]
+    T, err, flags = run(rgf, name, idx, rgf.RGF_FP64)
+    assert np.all(flags == 0), idx[flags != 0]
+    bar = FP64_REL * np.maximum(np.abs(T_x), 1e-6)
+    ratio = np.abs(T - T_x) / bar
+    assert ratio.max() <= 1.0, (idx[np.argmax(ratio)], ratio.max())

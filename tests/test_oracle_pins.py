@@ -279,3 +279,21 @@ def test_decimation_stops_and_counts():
     assert ok and 10 <= it <= 60
     g2, it2, ok2 = o.sancho_rubio(a, alpha, beta, max_iter=3)
     assert not ok2 and it2 == 3
+
+
+def test_newton_refinement_drops_a_diverging_step():
+    """Started from the advanced root of the uniform chain (|g alpha| > 1) the
+    Newton step's doubling grows instead of converging: the step is dropped,
+    g comes back unchanged and the refinement reports failure.  From the
+    retarded root it holds and changes nothing."""
+    z = complex(0.7, 1e-3)
+    lam = chain_lambda(z, 0.0, 1.0)
+    a = np.array([[z]], dtype=np.complex128)
+    one = np.array([[1.0 + 0j]])
+    g_adv = np.array([[1.0 / lam]])  # the other root of t l^2 - z l + t = 0: |g t| > 1
+    assert abs(g_adv[0, 0]) > 1.0
+    g, ok = o.newton_refine(a, one, one, g_adv.copy())
+    assert not ok and np.array_equal(g, g_adv)
+    g_ret = np.array([[lam]])
+    g2, ok2 = o.newton_refine(a, one, one, g_ret.copy())
+    assert ok2 and abs(g2[0, 0] - lam) <= 1e-14
