@@ -197,8 +197,9 @@ static int sancho_rubio(cplx *gs, const cplx *a, cplx *alpha, cplx *beta, int b,
  * the lead's original couplings (not the decimated ones).  work: 9 bb.  A step
  * whose doubling grows (|A|_F |B|_F above 1e4 times its first value, not
  * finite, or not below tol after 200 doublings) is dropped and the function
- * returns 0 with g as it was; a second step follows only when the first
- * correction exceeded 1e-10 |g|_F.  Returns 1 when the refinement held. */
+ * returns 0 with g as it was; another step follows while the last correction
+ * exceeded 1e-14 |g|_F (what a correction c leaves is of order K c^2, K up to
+ * ~1e6).  Returns 1 when the refinement held. */
 static int newton_refine(cplx *g, const cplx *a, const cplx *alpha, const cplx *beta, int b, real tol,
                          int steps, cplx *work) {
     size_t bb = (size_t)b * b;
@@ -231,7 +232,7 @@ static int newton_refine(cplx *g, const cplx *a, const cplx *alpha, const cplx *
         }
         if (!converged) return 0;
         for (size_t e = 0; e < bb; ++e) { g[e].re += X[e].re; g[e].im += X[e].im; }
-        if (fro(X, b) <= 1e-10L * fro(g, b)) break;
+        if (fro(X, b) <= 1e-14L * fro(g, b)) break;
     }
     return 1;
 }

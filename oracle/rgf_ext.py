@@ -70,7 +70,7 @@ def _lead_ptrs(lead, keep):
     return (ctypes.POINTER(ctypes.c_double) * 6)(*[_ptr(a) for a in arrs])
 
 
-def transmission(dev, energies, eta, tol=1e-18, max_iter=120, newton_steps=2, threads=None,
+def transmission(dev, energies, eta, tol=1e-18, max_iter=120, newton_steps=3, threads=None,
                  return_info=False):
     """T(E) in extended precision, rounded to float64 at the end.
 
@@ -102,7 +102,7 @@ def transmission(dev, energies, eta, tol=1e-18, max_iter=120, newton_steps=2, th
     return T
 
 
-def surface_gf(lead, side, E, eta, tol=1e-18, max_iter=120, newton_steps=2):
+def surface_gf(lead, side, E, eta, tol=1e-18, max_iter=120, newton_steps=3):
     """Surface Green's function of one lead (side 'L' or 'R') as (hi, lo)
     complex128 pairs: hi + lo is the 80-bit result to about 2^-64.  Returns
     (hi, lo, iterations); iterations < 0 means not converged."""

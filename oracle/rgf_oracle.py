@@ -96,8 +96,8 @@ def sancho_rubio(a, alpha, beta, tol=1e-14, max_iter=100):
     return _inv(eps_s), max_iter, False
 
 
-def newton_refine(a, alpha, beta, g, max_steps=2, tol=1e-28, max_doublings=100, growth=1e4,
-                  again=1e-8):
+def newton_refine(a, alpha, beta, g, max_steps=3, tol=1e-28, max_doublings=100, growth=1e4,
+                  again=1e-12):
     """Newton steps on g = (a - alpha g beta)^-1.  Returns (g, ok).
 
     One step: r = (a - alpha g beta) g - I; the correction X solves the
@@ -108,9 +108,11 @@ def newton_refine(a, alpha, beta, g, max_steps=2, tol=1e-28, max_doublings=100, 
     retarded fixed point; a g far enough from it can break that (near band
     edges at small eta), and the sums then grow: when p exceeds growth times
     its first value, turns non-finite or has not reached tol after
-    max_doublings, the step is dropped, g is kept and ok is False.  A second
-    step follows only when the first correction exceeded again |g|_F (Newton
-    converges quadratically, so a smaller one leaves nothing to correct)."""
+    max_doublings, the step is dropped, g is kept and ok is False.  Another
+    step follows while the last correction exceeded again |g|_F: Newton
+    converges quadratically, so what a correction of size c leaves is of
+    order K c^2 (K up to ~1e6 near band edges at eta = 1e-6), below the FP64
+    level for c <= 1e-12."""
     n = a.shape[0]
     eye = np.eye(n, dtype=np.complex128)
     for _ in range(max_steps):
@@ -140,7 +142,7 @@ def newton_refine(a, alpha, beta, g, max_steps=2, tol=1e-28, max_doublings=100, 
     return g, True
 
 
-def self_energies(dev, z, tol=1e-14, max_iter=100, newton_steps=2):
+def self_energies(dev, z, tol=1e-14, max_iter=100, newton_steps=3):
     """Sigma_L, Sigma_R, Gamma_L, Gamma_R, the decimation iteration counts and
     whether each lead's Newton refinement held (refined = (left, right))."""
     aL, alL, beL, cLlow, cLup = lead_blocks(dev.lead_L, z, "L")
@@ -259,7 +261,7 @@ def caroli(gamma_L, G1N, gamma_R):
 
 
 def transmission(dev, energies, eta, method="rgf", tol=1e-14, max_iter=100,
-                 return_info=False, newton_steps=2):
+                 return_info=False, newton_steps=3):
     """T(E) for each energy.  method: 'rgf' (left sweep), 'rgf_right'
     (mirror sweep) or 'dense' (full inversion)."""
     energies = np.asarray(energies, dtype=np.float64)

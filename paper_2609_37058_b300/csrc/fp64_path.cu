@@ -113,9 +113,11 @@ rgf_status fp64_decimate(rgf_plan_s* p, int W, const int* mask, double2* pool_ba
     // |A|_F |B|_F <= dec_tol^2.  A doubling that grows instead (above 1e4
     // times its first value: a g outside Newton's basin, near band edges at
     // small eta) drops the step: g keeps its decimation value and the energy
-    // is flagged RGF_FLAG_LEAD_NEWTON.  A second step follows for the entries
-    // whose correction exceeded 1e-8 |g|_F.  a, alpha and beta are formed
-    // again (the decimation overwrote them).
+    // is flagged RGF_FLAG_LEAD_NEWTON.  Another step (up to three) follows for
+    // the entries whose correction exceeded 1e-10 |g|_F: what a correction c
+    // leaves is of order K c^2 (K up to ~1e6 near band edges), below the FP64
+    // bar's need for c <= 1e-10.  a, alpha and beta are formed again (the
+    // decimation overwrote them).
     {
         double2 *a0 = pool.at(0), *al0 = pool.at(2), *be0 = pool.at(4), *Wm = pool.at(6), *r = pool.at(10);
         double2 *A = pool.at(12), *B = pool.at(14), *X = pool.at(16), *u1 = pool.at(18), *u2 = pool.at(20);
@@ -130,7 +132,7 @@ rgf_status fp64_decimate(rgf_plan_s* p, int W, const int* mask, double2* pool_ba
         RGF_TRY(form_f64(W, 2, b, E, eta, al, al0, nullptr, 0.0, nm, st));
         RGF_TRY(form_f64(W, 2, b, E, eta, be, be0, nullptr, 0.0, nm, st));
         const double stol = p->opt.dec_tol * p->opt.dec_tol;
-        for (int step = 0; step < 2; ++step) {
+        for (int step = 0; step < 3; ++step) {
             RGF_TRY(zgemm_f64(gemm_sq(W2, b, one, al0, g, u1, nm), st));   // alpha g
             RGF_TRY(zgemm_f64(gemm_sq(W2, b, one, u1, be0, u2, nm), st));  // alpha g beta
             RGF_TRY(sub_f64(W2, b, a0, u2, Wm, nm, st));
@@ -161,7 +163,7 @@ rgf_status fp64_decimate(rgf_plan_s* p, int W, const int* mask, double2* pool_ba
                 if (*p->h_remaining == 0) break;
             }
             RGF_CUDA_TRY(cudaMemsetAsync(p->d_remaining, 0, sizeof(int), st));
-            RGF_TRY(newton_finish_f64(W2, b, X, g, nm, p->d_status, 1e-8, nx, p->d_dec_flags, p->d_remaining, st));
+            RGF_TRY(newton_finish_f64(W2, b, X, g, nm, p->d_status, 1e-10, nx, p->d_dec_flags, p->d_remaining, st));
             RGF_CUDA_TRY(cudaMemcpyAsync(p->h_remaining, p->d_remaining, sizeof(int), cudaMemcpyDeviceToHost, st));
             RGF_CUDA_TRY(cudaStreamSynchronize(st));
             if (*p->h_remaining == 0) break;

@@ -238,7 +238,10 @@ rgf_status hp_decimate_run(const Ctx& c, int W, double tol, int max_iter, double
 // correction); g += X.  A doubling that grows instead (above 1e4 times its
 // first value) drops the step: g keeps its decimation value and the entry is
 // flagged RGF_FLAG_LEAD_NEWTON.  A second step follows for the entries whose
-// correction exceeded 1e-8 |g|_F.  Uses decimation-pool units 0..7, 10..17.
+// correction exceeded 1e-8 |g|_F (what a correction c leaves is of order
+// K c^2 with K up to ~1e6, far below the mixed path's 1e-6 bar in T; the FP64
+// path, held to 1e-9, takes up to three steps at 1e-10).  Uses
+// decimation-pool units 0..7, 10..17.
 rgf_status hp_newton_step(const Ctx& c, int W, double stol, int max_iter, const double2* a0, const double2* al0,
                           const double2* be0, double2* g) {
     MixedState* m = c.m;

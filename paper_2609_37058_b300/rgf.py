@@ -25,7 +25,7 @@ STATUS_NAMES = ["RGF_OK", "RGF_E_INVALID", "RGF_E_OOM", "RGF_E_CUDA", "RGF_E_NOT
 RGF_FP64, RGF_MIXED = 0, 1
 RGF_MEM_HOST, RGF_MEM_DEVICE = 0, 1
 RGF_LEAD_LEFT, RGF_LEAD_RIGHT = 0, 1
-RGF_FLAG_NOCONV_L, RGF_FLAG_NOCONV_R, RGF_FLAG_SINGULAR, RGF_FLAG_REFINE = 1, 2, 4, 8
+RGF_FLAG_NOCONV_L, RGF_FLAG_NOCONV_R, RGF_FLAG_SINGULAR, RGF_FLAG_REFINE, RGF_FLAG_LEAD_NEWTON = 1, 2, 4, 8, 16
 
 
 class RGFError(RuntimeError):
