@@ -4,7 +4,9 @@
 #pragma once
 
 #include <atomic>
+#include <mutex>
 #include <type_traits>
+#include <vector>
 
 #include "kernels.h"
 
@@ -21,6 +23,37 @@ template <> struct CT<float2> {
 };
 
 __host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+
+// Raises a kernel's dynamic shared-memory limit once per function pointer.
+// A kernel template instantiated from this header in several translation
+// units is registered once per unit, and a launch uses its own unit's
+// registration, so the limit is tracked per pointer, not per kernel.
+inline rgf_status smem_limit_once(const void* fn, int bytes) {
+    static std::mutex mu;
+    static std::vector<const void*> done;
+    std::lock_guard<std::mutex> lock(mu);
+    for (const void* f : done)
+        if (f == fn) return RGF_OK;
+    RGF_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    done.push_back(fn);
+    return RGF_OK;
+}
+
+// x = o[0] + o[1] + o[2] within 2^-24 |x|: each BF16 value is the rounded
+// remainder, and the remainders x - o[0] and x - o[0] - o[1] are exact in FP32.
+__device__ __forceinline__ void split3_bf16(float x, __nv_bfloat16 (&o)[kGjSplits]) {
+    o[0] = __float2bfloat16_rn(x);
+    float r = x - __bfloat162float(o[0]);
+    o[1] = __float2bfloat16_rn(r);
+    r -= __bfloat162float(o[1]);
+    o[2] = __float2bfloat16_rn(r);
+}
+__device__ __forceinline__ void store_bf2(__nv_bfloat16* p, __nv_bfloat16 x, __nv_bfloat16 y) {
+    __nv_bfloat162 v;
+    v.x = x;
+    v.y = y;
+    *reinterpret_cast<__nv_bfloat162*>(p) = v;
+}
 
 // 64 x 64 complex output tile per CTA, K step 16, 256 threads each owning a
 // 4 x 4 set of outputs strided by 16 so shared-memory reads are broadcasts
@@ -232,8 +265,8 @@ __device__ __forceinline__ T2 shfl_c(T2 v, int src) {
 // barrier; search of the next column by all 256 threads; barrier.
 constexpr int GJ_WARPS = 8;
 template <typename T2, int NB>
-__global__ void __launch_bounds__(256) k_gj_panel(int b, int k0, int nbk, T2* A, long sA, T2* Pbar, int* piv,
-                                                  int* flags, const int* active) {
+__global__ void __launch_bounds__(256) k_gj_panel(int b, int k0, int nbk, T2* A, long sA, T2* Pbar,
+                                                  __nv_bfloat16* Ps, int* piv, int* flags, const int* active) {
     using C = CT<T2>;
     using R = typename C::R;
     constexpr int P = NB + 1, NW = GJ_WARPS;
@@ -337,6 +370,26 @@ __global__ void __launch_bounds__(256) k_gj_panel(int b, int k0, int nbk, T2* A,
             __syncthreads();
         }
     }
+    if constexpr (std::is_same<T2, float2>::value) {
+        if (Ps) {
+            // Tensor-core update: Pbar as BF16 splits (zero beyond nbk).
+            __nv_bfloat16* Pq = Ps + (long)bi * kGjSplits * b * kGjKp;
+            for (int r = wid; r < b; r += NW) {
+                float2 v = make_float2(0.f, 0.f);
+                if (col_ok) {
+                    v = pan[r * P + lane];
+                    Ab[(long)r * b + k0 + lane] = v;
+                    if (r == k0 + lane) v.x -= 1.0f;
+                }
+                __nv_bfloat16 re[kGjSplits], im[kGjSplits];
+                split3_bf16(v.x, re);
+                split3_bf16(v.y, im);
+#pragma unroll
+                for (int s = 0; s < kGjSplits; ++s) store_bf2(Pq + ((long)s * b + r) * kGjKp + 2 * lane, re[s], im[s]);
+            }
+            return;
+        }
+    }
     T2* Pb = Pbar + (long)bi * b * nbk;
     if (col_ok) {
         for (int r = wid; r < b; r += NW) {
@@ -355,7 +408,7 @@ __global__ void __launch_bounds__(256) k_gj_panel(int b, int k0, int nbk, T2* A,
 // rows back, so the global accesses are coalesced and independent.
 template <typename T2>
 __global__ void __launch_bounds__(256) k_gj_swap(int b, int k0, int nbk, T2* A, long sA, const int* piv, T2* T,
-                                                 const int* active) {
+                                                 __nv_bfloat16* Ts, const int* active) {
     const int bi = blockIdx.y;
     if (active && !active[bi]) return;
     __shared__ int rows[64];
@@ -407,6 +460,33 @@ __global__ void __launch_bounds__(256) k_gj_swap(int b, int k0, int nbk, T2* A, 
         }
     }
     __syncthreads();
+    if constexpr (std::is_same<T2, float2>::value) {
+        if (Ts) {
+            if (ok)
+                for (int q = wid; q < n; q += 8) Ab[(long)rows[q] * b + c] = tile[q][lane];
+            // T as BF16 splits in the B layout of the K-interleaved complex
+            // product (zero in the panel's columns and beyond nbk): a warp
+            // per column, lane = row of T, so each warp store is 128
+            // contiguous bytes of one output row.
+            __nv_bfloat16* Tq = Ts + (long)bi * kGjSplits * 2 * b * kGjKp;
+            for (int cl = wid; cl < 32; cl += 8) {
+                const int cc = blockIdx.x * 32 + cl;
+                if (cc >= b) break;
+                const bool pc = cc >= k0 && cc < k0 + nbk;
+                const float2 t = (!pc && lane < nbk) ? tile[lane][cl] : make_float2(0.f, 0.f);
+                __nv_bfloat16 re[kGjSplits], im[kGjSplits];
+                split3_bf16(t.x, re);
+                split3_bf16(t.y, im);
+#pragma unroll
+                for (int s = 0; s < kGjSplits; ++s) {
+                    __nv_bfloat16* o = Tq + ((long)s * 2 * b + 2 * cc) * kGjKp + 2 * lane;
+                    store_bf2(o, re[s], __hneg(im[s]));
+                    store_bf2(o + kGjKp, im[s], re[s]);
+                }
+            }
+            return;
+        }
+    }
     if (c >= b) return;
     if (in_panel) {
         for (int jj = wid; jj < nbk; jj += 8) Tb[(long)jj * b + c] = CT<T2>::make(0, 0);
@@ -452,15 +532,25 @@ __global__ void __launch_bounds__(256) k_gj_unpermute(int b, T2* A, long sA, con
 // nb_override (16, or 32 where that is the default) replaces the default
 // panel width for b >= 64; 0 keeps it.  The workspace is sized for the
 // default, which is never narrower.
+// tc_status (complex64 only): non-null selects the tensor-core trailing
+// update (gj_update_tc; ws laid out as Pbar splits, T splits, pivots).
 template <typename T2>
 rgf_status inv_t(int batch, int b, T2* A, long sA, void* ws, int* flags, const int* active, cudaStream_t st,
-                 int nb_override = 0) {
+                 int nb_override = 0, int* tc_status = nullptr) {
     if (batch <= 0) return RGF_OK;
     int nb = gj_nb(b);
     if (b >= 64 && (nb_override == 16 || (nb_override == 32 && nb == 32))) nb = nb_override;
+    const bool tc = std::is_same<T2, float2>::value && tc_status != nullptr;
     T2* Pbar = (T2*)ws;
     T2* T = Pbar + (size_t)batch * b * nb;
     int* piv = (int*)(T + (size_t)batch * b * nb);
+    __nv_bfloat16* Ps = nullptr;
+    __nv_bfloat16* Ts = nullptr;
+    if (tc) {
+        Ps = (__nv_bfloat16*)ws;
+        Ts = Ps + (size_t)batch * kGjSplits * b * kGjKp;
+        piv = (int*)(Ts + (size_t)batch * kGjSplits * 2 * b * kGjKp);
+    }
     const size_t smem = ((size_t)b * (nb + 1) + b) * sizeof(T2);
     if (smem > 200 * 1024) {
         set_error("inverse: b = %d needs %zu bytes of shared memory", b, smem);
@@ -472,29 +562,24 @@ rgf_status inv_t(int batch, int b, T2* A, long sA, void* ws, int* flags, const i
         return RGF_E_INVALID;
     }
     if (b < 32) panel = k_gj_panel<T2, 32>;  // nb = b < 32 columns of a 32-lane panel
-    if (smem > 48 * 1024) {
-        // One fixed limit for every block size, set once per panel width:
-        // the attribute belongs to the function, and host threads inverting
-        // different sizes share it.  (Set once, it is not repeated inside a
-        // stream capture.)
-        static std::atomic<bool> done[2] = {false, false};
-        std::atomic<bool>& d = done[panel == k_gj_panel<T2, 16> ? 1 : 0];
-        if (!d.load()) {
-            RGF_CUDA_TRY(cudaFuncSetAttribute(panel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-            d.store(true);
-        }
-    }
+    // One fixed limit for every block size (host threads inverting
+    // different sizes share the function).
+    if (smem > 48 * 1024) RGF_TRY(smem_limit_once(reinterpret_cast<const void*>(panel), 200 * 1024));
     const int pitch_nb = (panel == k_gj_panel<T2, 16>) ? 16 : 32;
     for (int k0 = 0; k0 < b; k0 += nb) {
         const int nbk = (b - k0) < nb ? (b - k0) : nb;
         const size_t sm = ((size_t)b * (pitch_nb + 1) + b) * sizeof(T2);
-        panel<<<batch, 256, sm, st>>>(b, k0, nbk, A, sA, Pbar, piv, flags, active);
+        panel<<<batch, 256, sm, st>>>(b, k0, nbk, A, sA, Pbar, Ps, piv, flags, active);
         RGF_LAUNCH_CHECK();
         if (nbk < b) {
             dim3 g2(ceil_div(b, 32), batch);
-            k_gj_swap<T2><<<g2, 256, 0, st>>>(b, k0, nbk, A, sA, piv, T, active);
+            k_gj_swap<T2><<<g2, 256, 0, st>>>(b, k0, nbk, A, sA, piv, T, Ts, active);
             RGF_LAUNCH_CHECK();
             if constexpr (std::is_same<T2, float2>::value) {
+                if (tc) {
+                    RGF_TRY(gj_update_tc(batch, b, nbk, Ps, Ts, A, sA, k0, k0 + nbk, active, tc_status, st));
+                    continue;
+                }
                 RGF_TRY(gj_update_f32(batch, b, b, nbk, Pbar, (long)b * nbk, T, (long)nbk * b, A, b, sA, k0,
                                       k0 + nbk, active, st));
                 continue;

@@ -99,13 +99,21 @@ rgf_status rgf_kernel_inverse_c64(int batch, int b, float* A, int* flags) {
     }
     if (batch == 0) return RGF_OK;
     const size_t nn = (size_t)b * b;
-    DevBuf dA, ws, df;
+    DevBuf dA, ws, df, dst;
     RGF_TRY(dalloc(dA, batch * nn * 8));
-    RGF_TRY(dalloc(ws, rgf::inv_workspace_bytes_t<float2>(batch, b)));
+    RGF_TRY(dalloc(ws, rgf::inv_c32_workspace_bytes(batch, b)));
     RGF_TRY(dalloc(df, batch * sizeof(int)));
+    RGF_TRY(dalloc(dst, sizeof(int)));
     RGF_CUDA_TRY(cudaMemcpy(dA.p, A, batch * nn * 8, cudaMemcpyHostToDevice));
     RGF_CUDA_TRY(cudaMemset(df.p, 0, batch * sizeof(int)));
-    RGF_TRY(rgf::inv_t<float2>(batch, b, (float2*)dA.p, (long)nn, ws.p, (int*)df.p, nullptr, 0));
+    RGF_CUDA_TRY(cudaMemset(dst.p, 0, sizeof(int)));
+    RGF_TRY(rgf::inv_c32(batch, b, (float2*)dA.p, (long)nn, ws.p, (int*)df.p, nullptr, (int*)dst.p, 0));
+    int status = 0;
+    RGF_CUDA_TRY(cudaMemcpy(&status, dst.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (status != 0) {
+        rgf::set_error("rgf_kernel_inverse_c64: tensor-core pipeline timed out (status 0x%x)", status);
+        return RGF_E_CUDA;
+    }
     RGF_CUDA_TRY(cudaMemcpy(A, dA.p, batch * nn * 8, cudaMemcpyDeviceToHost));
     if (flags) RGF_CUDA_TRY(cudaMemcpy(flags, df.p, batch * sizeof(int), cudaMemcpyDeviceToHost));
     return RGF_OK;

@@ -1,6 +1,8 @@
 // Kernel launch wrappers of the RGF library (host-callable, stream-ordered).
 #pragma once
 
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 
 namespace rgf {
@@ -45,6 +47,30 @@ rgf_status zgemm_f64(const ZGemm& g, cudaStream_t st);
 size_t inv_f64_workspace_bytes(int batch, int b);
 rgf_status inv_f64(int batch, int b, double2* A, long sA, void* ws, int* flags,
                    const int* active, cudaStream_t st);
+
+// In-place batched inverse of b x b complex64 matrices (the mixed path's
+// seed): the same blocked Gauss-Jordan elimination, with each trailing
+// update C += Pbar T on the tensor cores.  Every FP32 value x of Pbar and
+// T is split into three BF16 values x0 = bf16(x), x1 = bf16(x - x0), x2 =
+// bf16(x - x0 - x1) (x = x0 + x1 + x2 within 2^-24 |x|); the six split
+// pairs i + j <= 2 are accumulated in FP32 (the dropped pairs are below
+// 2^-23 of the product), i.e. the update is FP32-accurate.  Layouts, per
+// batch entry and split, kGjKp BF16 per row, K index 2 j + (0 re, 1 im):
+//   Pbar splits [split][b rows][kGjKp]: (Re, Im) of Pbar[r][j];
+//   T splits [split][2b rows][kGjKp]: row 2c = (Re T[j][c], -Im T[j][c]),
+//   row 2c + 1 = (Im T[j][c], Re T[j][c]).
+// status: the tensor-core pipeline's wait-timeout word (bits set on a
+// timeout); null selects the CUDA-core update.  RGF_GJ_TC=0 in the
+// environment (read once) selects it too.
+constexpr int kGjSplits = 3;
+constexpr int kGjKp = 64;
+size_t inv_c32_workspace_bytes(int batch, int b);
+rgf_status inv_c32(int batch, int b, float2* A, long sA, void* ws, int* flags, const int* active, int* status,
+                   cudaStream_t st, int nb_override = 0);
+// One trailing update: C[:, not in [skip0, skip1)] += Pbar T from the splits
+// (nbk <= 32 columns of Pbar; K padded with zeros to kGjKp).
+rgf_status gj_update_tc(int batch, int b, int nbk, const __nv_bfloat16* Ps, const __nv_bfloat16* Ts, float2* C,
+                        long sC, int skip0, int skip1, const int* active, int* status, cudaStream_t st);
 
 // Elementwise helpers (batch of b x b matrices, stride b*b).
 rgf_status set_identity_f64(int batch, int b, double2* A, cudaStream_t st);

@@ -110,7 +110,7 @@ rgf_status inv_hp(const Ctx& c, int cnt, int W, const double2* M, double2* X, do
                   int* gj_flags, const double2* X_prev) {
     MixedState* m = c.m;
     RGF_TRY(c128_to_c64(cnt, c.b, M, m->c64, act, c.st));
-    RGF_TRY(inv_t<float2>(cnt, c.b, m->c64, c.nn, m->inv_ws, nullptr, act, c.st));
+    RGF_TRY(inv_c32(cnt, c.b, m->c64, c.nn, m->inv_ws, nullptr, act, m->status, c.st));
     RGF_TRY(c64_to_c128(cnt, c.b, m->c64, X, act, c.st));
     const int steps = c.ns_steps;
     if (steps == 0) return RGF_OK;
@@ -324,7 +324,7 @@ rgf_status inv_mixed_steps(const Ctx& c, int cnt, int W, const float4* M, float4
         RGF_TRY(dfc_hi_to_c64(cnt, c.b, M, m->c64, act, c.st));
         // An FP32 seed with a zero pivot is not reported: its residual is not
         // finite, so it is reseeded in FP64 below, which reports its own pivots.
-        RGF_TRY(inv_t<float2>(cnt, c.b, m->c64, c.nn, m->inv_ws, nullptr, act, c.st, m->gj_nb));
+        RGF_TRY(inv_c32(cnt, c.b, m->c64, c.nn, m->inv_ws, nullptr, act, m->status, c.st, m->gj_nb));
         RGF_TRY(c64_to_dfc(cnt, c.b, m->c64, X, act, c.st));
         if (steps == 0) return RGF_OK;
         RGF_TRY(mask_init(cnt, act, m->nsact[0], c.st));
@@ -387,7 +387,7 @@ size_t mixed_workspace_bytes(int W, int b, int slice_entries, int inv_entries) {
     const size_t nn = (size_t)b * b;
     size_t s = (size_t)kPoolUnits * W * nn * sizeof(float4);
     s += 2 * sa_bytes(slice_entries, b, Kp) + 2 * sb_bytes(slice_entries, b, Kp);
-    s += (size_t)inv_entries * nn * sizeof(float2) + inv_workspace_bytes_t<float2>(inv_entries, b);
+    s += (size_t)inv_entries * nn * sizeof(float2) + inv_c32_workspace_bytes(inv_entries, b);
     s += (size_t)inv_entries * nn * sizeof(double2) + inv_workspace_bytes_t<double2>(inv_entries, b);
     s += (size_t)inv_entries * 4 * sizeof(int) +
          (size_t)inv_entries * sizeof(double2) + 8192;
@@ -442,7 +442,7 @@ rgf_status mixed_state_init(MixedState* m, int b, int W, void* ws, cudaStream_t 
     m->c64 = (float2*)w;
     w += (size_t)inv_entries * nn * sizeof(float2);
     m->inv_ws = (void*)w;
-    w += inv_workspace_bytes_t<float2>(inv_entries, b);
+    w += inv_c32_workspace_bytes(inv_entries, b);
     w = (char*)(((uintptr_t)w + 255) & ~(uintptr_t)255);
     m->c128 = (double2*)w;
     w += (size_t)inv_entries * nn * sizeof(double2);

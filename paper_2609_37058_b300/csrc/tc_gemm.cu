@@ -31,6 +31,12 @@ namespace rgf {
 namespace {
 constexpr int TC_BM = 128;
 constexpr uint32_t TC_TMEM_COLS = 512;
+// Per-epilogue-warp transpose buffer of the FP32 update (kOutC32): 32 rows
+// of 16 floats, pitch 18 (8-byte aligned float2 accesses), after the
+// barriers; eight epilogue warps.
+constexpr int kC32Pitch = 18;
+constexpr int kC32Warp = 32 * kC32Pitch;
+constexpr int kC32Smem = 8 * kC32Warp * 4;
 
 // Tile configuration of one kernel variant: NSL slices per operand, NGRP
 // TMEM accumulators (groups 0..NGRP-2 exact, the last one the tail), BN real
@@ -219,19 +225,29 @@ struct TcArgs {
     // loads of the first K chunk so that the pipeline's waits run out.
     unsigned long long wait_ns;
     int skip_first_chunk;
+    int skip0, skip1;  // complex columns left alone (kOutC32)
 };
 
-// Output element: double-float complex (float4) or FP64 complex (double2).
-template <bool OUT64>
-using OutT = typename std::conditional<OUT64, double2, float4>::type;
+// Output modes: double-float complex (float4), FP64 complex (double2), or
+// FP32 complex (float2; one accumulator, for the FP32 seed inverse's
+// trailing updates, which also skip the columns [skip0, skip1)).
+constexpr int kOutDF = 0, kOutF64 = 1, kOutC32 = 2;
+template <int OM> struct OutSel { using T = float4; };
+template <> struct OutSel<kOutF64> { using T = double2; };
+template <> struct OutSel<kOutC32> { using T = float2; };
+template <int OM>
+using OutT = typename OutSel<OM>::T;
 
 // The 8 complex values (16 real accumulator columns) one lane holds for one
 // row: group sums combined, sign applied.
-template <int NGRP, bool OUT64>
-__device__ __forceinline__ void combine_chunk(const TcArgs& g, const float (&v)[NGRP][16], OutT<OUT64> (&res)[8]) {
+template <int NGRP, int OM>
+__device__ __forceinline__ void combine_chunk(const TcArgs& g, const float (&v)[NGRP][16], OutT<OM> (&res)[8]) {
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
-        if constexpr (OUT64) {
+        if constexpr (OM == kOutC32) {
+            const float sg = g.alpha < 0.0f ? -1.0f : 1.0f;
+            res[t] = make_float2(sg * v[0][2 * t], sg * v[0][2 * t + 1]);
+        } else if constexpr (OM == kOutF64) {
             double re = sum_groups_f64<NGRP>(v, 2 * t);
             double im = sum_groups_f64<NGRP>(v, 2 * t + 1);
             if (g.alpha < 0.0f) {
@@ -252,15 +268,24 @@ __device__ __forceinline__ void combine_chunk(const TcArgs& g, const float (&v)[
 }
 
 // Addend and identity of those values and their store: row r, columns from cb.
-template <bool OUT64>
-__device__ __forceinline__ void finish_chunk(const TcArgs& g, const OutT<OUT64> (&res)[8], int bi, int r, int cb) {
+template <int OM>
+__device__ __forceinline__ void finish_chunk(const TcArgs& g, const OutT<OM> (&res)[8], int bi, int r, int cb) {
     if (r >= g.m) return;
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
         const int c = cb + t;
         if (c >= g.n) continue;
         const long o = (long)bi * g.sC + (long)r * g.n + c;
-        if constexpr (OUT64) {
+        if constexpr (OM == kOutC32) {
+            if (c >= g.skip0 && c < g.skip1) continue;
+            float2 x = res[t];
+            if (g.D) {
+                const float2 d = reinterpret_cast<const float2*>(g.D)[(long)bi * g.sD + (long)r * g.n + c];
+                x.x += d.x;
+                x.y += d.y;
+            }
+            reinterpret_cast<float2*>(g.C)[o] = x;
+        } else if constexpr (OM == kOutF64) {
             double re = res[t].x, im = res[t].y;
             if (g.D) {
                 const double2 d = reinterpret_cast<const double2*>(g.D)[(long)bi * g.sD + (long)r * g.n + c];
@@ -282,11 +307,11 @@ __device__ __forceinline__ void finish_chunk(const TcArgs& g, const OutT<OUT64> 
     }
 }
 
-template <int NGRP, bool OUT64>
+template <int NGRP, int OM>
 __device__ __forceinline__ void store_chunk(const TcArgs& g, const float (&v)[NGRP][16], int bi, int r, int cb) {
-    OutT<OUT64> res[8];
-    combine_chunk<NGRP, OUT64>(g, v, res);
-    finish_chunk<OUT64>(g, res, bi, r, cb);
+    OutT<OM> res[8];
+    combine_chunk<NGRP, OM>(g, v, res);
+    finish_chunk<OM>(g, res, bi, r, cb);
 }
 
 // MMAs of one K chunk in stage buffer st: the slice pairs (i, j), i + j <=
@@ -320,7 +345,7 @@ __device__ __forceinline__ void mma_chunk(const unsigned char* st, uint32_t tadd
     }
 }
 
-template <int NSL, int NGRP, int BN, bool OUT64, int BK, int PL>
+template <int NSL, int NGRP, int BN, int OM, int BK, int PL>
 __global__ void __launch_bounds__(256, 1)
     k_oz_tc(TcArgs g, const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB) {
     using Cfg = TcCfg<NSL, NGRP, BN, BK>;
@@ -408,7 +433,7 @@ __global__ void __launch_bounds__(256, 1)
 #pragma unroll
             for (int gq = 0; gq < NGRP; ++gq) tmem_ld16(trow + gq * BN + q * 16, v[gq]);
             tmem_ld_wait();
-            store_chunk<NGRP, OUT64>(g, v, bi, r, (n0 + q * 16) >> 1);
+            store_chunk<NGRP, OM>(g, v, bi, r, (n0 + q * 16) >> 1);
         }
     }
     tc_fence_before();
@@ -433,7 +458,7 @@ __global__ void __launch_bounds__(256, 1)
 // the MMA issuer starts the next tile as soon as every epilogue warp has
 // read and combined its chunks (the accumulators are single-buffered:
 // NGRP * BN of the 512 columns); addends and stores follow.
-template <int NSL, int NGRP, int BN, bool OUT64, int BK, int PL>
+template <int NSL, int NGRP, int BN, int OM, int BK, int PL>
 __global__ void __launch_bounds__(320, 1)
     k_oz_tc_p(TcArgs g, const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB) {
     using Cfg = TcCfg<NSL, NGRP, BN, BK>;
@@ -443,7 +468,7 @@ __global__ void __launch_bounds__(320, 1)
     // Results of all chunks held in registers until the accumulators are
     // released: only where they fit in the 168 registers a thread of a
     // ten-warp CTA gets (the double-float tiles of width 64 and 96).
-    constexpr bool kDefer = !OUT64 && BN != 80;
+    constexpr bool kDefer = OM == kOutDF && BN != 80;
     static_assert(NQ >= 2, "every epilogue warp needs a chunk");
     extern __shared__ __align__(1024) unsigned char smem_tc[];
     unsigned char* base = (unsigned char*)(((uintptr_t)smem_tc + 1023) & ~(uintptr_t)1023);
@@ -553,13 +578,72 @@ __global__ void __launch_bounds__(320, 1)
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
             const int bx = t % ntx, by = (t / ntx) % nty, bi = t / (ntx * nty);
             if (g.active && !g.active[bi]) continue;
+            const int r = by * TC_BM + quad * 32 + lane;
+            if constexpr (OM == kOutC32) {
+                // In-place FP32 update C += A B.  A lane holds one row of a
+                // 16-column chunk; the chunk goes through a per-warp
+                // shared-memory transpose so that each access covers four rows
+                // of 64 contiguous bytes (lane: row sub + 4 s, complex column
+                // col8), i.e. whole sectors.  The addends do not depend on the
+                // MMAs and are loaded before the wait for the accumulators.
+                const int row0 = by * TC_BM + quad * 32;
+                const int sub = lane >> 3, col8 = lane & 7;
+                float* tb = reinterpret_cast<float*>(base + S * Cfg::STAGE + 256) + (warp - 2) * kC32Warp;
+                float2 dv[NCH][8];
+#pragma unroll
+                for (int k = 0; k < NCH; ++k) {
+                    const int c = ((bx * BN + (half + 2 * k) * 16) >> 1) + col8;
+#pragma unroll
+                    for (int s8 = 0; s8 < 8; ++s8) {
+                        const int rr = row0 + sub + 4 * s8;
+                        const bool in = g.D && half + 2 * k < NQ && rr < g.m && c < g.n;
+                        dv[k][s8] = in ? reinterpret_cast<const float2*>(g.D)[(long)bi * g.sD + (long)rr * g.n + c]
+                                       : make_float2(0.f, 0.f);
+                    }
+                }
+                int ok_c = 0;
+                if (lane == 0) ok_c = (mbar_wait(acc_full, lt & 1, status, 0x4, g.wait_ns) && !*s_fail) ? 1 : 0;
+                if (__shfl_sync(0xffffffffu, ok_c, 0) == 0) break;
+                tc_fence_after();
+                const float sg = g.alpha < 0.0f ? -1.0f : 1.0f;
+#pragma unroll
+                for (int k = 0; k < NCH; ++k) {
+                    const int q = half + 2 * k;
+                    if (q >= NQ) continue;
+                    float v[16];
+                    tmem_ld16(trow + q * 16, v);
+                    tmem_ld_wait();
+                    if (q + 2 >= NQ) {
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(acc_empty);
+                    }
+#pragma unroll
+                    for (int t = 0; t < 8; ++t)
+                        *reinterpret_cast<float2*>(tb + lane * kC32Pitch + 2 * t) =
+                            make_float2(sg * v[2 * t], sg * v[2 * t + 1]);
+                    __syncwarp();
+                    const int c = ((bx * BN + q * 16) >> 1) + col8;
+                    const bool c_ok = c < g.n && !(c >= g.skip0 && c < g.skip1);
+#pragma unroll
+                    for (int s8 = 0; s8 < 8; ++s8) {
+                        const int rr = row0 + sub + 4 * s8;
+                        const float2 x = *reinterpret_cast<const float2*>(tb + (sub + 4 * s8) * kC32Pitch + 2 * col8);
+                        if (c_ok && rr < g.m)
+                            reinterpret_cast<float2*>(g.C)[(long)bi * g.sC + (long)rr * g.n + c] =
+                                make_float2(x.x + dv[k][s8].x, x.y + dv[k][s8].y);
+                    }
+                    __syncwarp();
+                }
+                ++lt;
+                continue;
+            }
             // One lane waits; the outcome is made warp-uniform because the
             // TMEM loads below are warp-collective.
             int ok_i = 0;
             if (lane == 0) ok_i = (mbar_wait(acc_full, lt & 1, status, 0x4, g.wait_ns) && !*s_fail) ? 1 : 0;
             if (__shfl_sync(0xffffffffu, ok_i, 0) == 0) break;
             tc_fence_after();
-            const int r = by * TC_BM + quad * 32 + lane;
             if constexpr (!kDefer) {
 #pragma unroll 1
                 for (int q = half; q < NQ; q += 2) {
@@ -574,7 +658,7 @@ __global__ void __launch_bounds__(320, 1)
                         __syncwarp();
                         if (lane == 0) mbar_arrive(acc_empty);
                     }
-                    store_chunk<NGRP, OUT64>(g, v, bi, r, (bx * BN + q * 16) >> 1);
+                    store_chunk<NGRP, OM>(g, v, bi, r, (bx * BN + q * 16) >> 1);
                 }
                 ++lt;
                 continue;
@@ -582,7 +666,7 @@ __global__ void __launch_bounds__(320, 1)
             // All of this warp's chunks are read and combined into registers
             // before the accumulators are released; the addends are read and
             // the results stored while the next tile's MMAs run.
-            OutT<OUT64> res[NCH][8];
+            OutT<OM> res[NCH][8];
 #pragma unroll
             for (int k = 0; k < NCH; ++k) {
                 const int q = half + 2 * k;
@@ -596,13 +680,13 @@ __global__ void __launch_bounds__(320, 1)
                         __syncwarp();
                         if (lane == 0) mbar_arrive(acc_empty);
                     }
-                    combine_chunk<NGRP, OUT64>(g, v, res[k]);
+                    combine_chunk<NGRP, OM>(g, v, res[k]);
                 }
             }
 #pragma unroll
             for (int k = 0; k < NCH; ++k) {
                 const int q = half + 2 * k;
-                if (q < NQ) finish_chunk<OUT64>(g, res[k], bi, r, (bx * BN + q * 16) >> 1);
+                if (q < NQ) finish_chunk<OM>(g, res[k], bi, r, (bx * BN + q * 16) >> 1);
             }
             ++lt;
         }
@@ -669,6 +753,9 @@ static rgf_status encode_slices(CUtensorMap* map, const __nv_bfloat16* ptr, int 
 // until the other has finished all its tiles).
 template <int SMEM>
 constexpr int kPersistSmem = SMEM > 116 * 1024 ? SMEM : 116 * 1024;
+// The FP32 update's persistent CTA also holds the epilogue transpose buffers.
+template <int SMEM, int OM>
+constexpr int kPersistSmemOf = kPersistSmem<SMEM + (OM == kOutC32 ? kC32Smem : 0)>;
 
 // Persistent tile loop (default) or one CTA per tile with
 // RGF_TC_PERSIST=0 in the environment (read once).
@@ -680,8 +767,8 @@ static bool tc_persistent() {
     return on;
 }
 
-template <int NSL, int NGRP, int BN, bool OUT64, int BK, int PL = NSL>
-static rgf_status launch_tc(const TcArgs& g, cudaStream_t st) {
+template <int NSL, int NGRP, int BN, int OM, int BK, int PL = NSL>
+static rgf_status launch_tc(const TcArgs& g, cudaStream_t st, bool count_work = true) {
     using Cfg = TcCfg<NSL, NGRP, BN, BK>;
     if (g.batch <= 0) return RGF_OK;
     if (g.Kp % BK != 0 || ((uintptr_t)g.As & 15) || ((uintptr_t)g.Bs & 15) || !g.status) {
@@ -698,10 +785,10 @@ static rgf_status launch_tc(const TcArgs& g, cudaStream_t st) {
     static std::atomic<bool> attr{false};
     if (!attr.load()) {
         // Idempotent: threads that race here all set the same value.
-        RGF_CUDA_TRY(cudaFuncSetAttribute(k_oz_tc<NSL, NGRP, BN, OUT64, BK, PL>,
+        RGF_CUDA_TRY(cudaFuncSetAttribute(k_oz_tc<NSL, NGRP, BN, OM, BK, PL>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM));
-        RGF_CUDA_TRY(cudaFuncSetAttribute(k_oz_tc_p<NSL, NGRP, BN, OUT64, BK, PL>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, kPersistSmem<Cfg::SMEM>));
+        RGF_CUDA_TRY(cudaFuncSetAttribute(k_oz_tc_p<NSL, NGRP, BN, OM, BK, PL>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, kPersistSmemOf<Cfg::SMEM, OM>));
         attr.store(true);
     }
     dim3 grid(ceil_div(2L * g.n, BN), ceil_div(g.m, TC_BM), g.batch);
@@ -711,14 +798,14 @@ static rgf_status launch_tc(const TcArgs& g, cudaStream_t st) {
     RGF_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     const bool persistent = tc_persistent() && ntiles < 0x7fffffffL;
     // Only unmasked launches are timed: their work is exactly known.
-    const bool timed = gemm_timing_enabled() && g.active == nullptr;
+    const bool timed = count_work && gemm_timing_enabled() && g.active == nullptr;
     cudaEvent_t ev = nullptr;
     if (timed) gemm_timing_before(st, &ev);
     if (persistent) {
         const int nblk = (int)(ntiles < nsm ? ntiles : nsm);
-        k_oz_tc_p<NSL, NGRP, BN, OUT64, BK, PL><<<nblk, 320, kPersistSmem<Cfg::SMEM>, st>>>(g, ta, tb);
+        k_oz_tc_p<NSL, NGRP, BN, OM, BK, PL><<<nblk, 320, kPersistSmemOf<Cfg::SMEM, OM>, st>>>(g, ta, tb);
     } else {
-        k_oz_tc<NSL, NGRP, BN, OUT64, BK, PL><<<grid, 256, Cfg::SMEM, st>>>(g, ta, tb);
+        k_oz_tc<NSL, NGRP, BN, OM, BK, PL><<<grid, 256, Cfg::SMEM, st>>>(g, ta, tb);
     }
     RGF_LAUNCH_CHECK();
     if (timed) {
@@ -750,36 +837,36 @@ rgf_status oz_gemm_tc(const OzGemm& g, cudaStream_t st) {
         // Four of the six slices (ten pairs, four exact groups): for
         // products whose result is a small correction (see OzGemm::nsl).
         switch (g.bn) {
-            case 64: return launch_tc<4, 4, 64, false, 32, kSlices>(a, st);
-            case 80: return launch_tc<4, 4, 80, false, 32, kSlices>(a, st);
+            case 64: return launch_tc<4, 4, 64, kOutDF, 32, kSlices>(a, st);
+            case 80: return launch_tc<4, 4, 80, kOutDF, 32, kSlices>(a, st);
             case 0:
-            case 96: return launch_tc<4, 4, 96, false, 32, kSlices>(a, st);
+            case 96: return launch_tc<4, 4, 96, kOutDF, 32, kSlices>(a, st);
             default: break;
         }
     } else if (g.nsl == 5) {
         // Five of the six slices (15 pairs, one accumulator per group; see
         // OzGemm::nsl): reached through the kernel-level entry point.
         switch (g.bn) {
-            case 64: return launch_tc<5, 5, 64, false, 32, kSlices>(a, st);
-            case 80: return launch_tc<5, 5, 80, false, 32, kSlices>(a, st);
+            case 64: return launch_tc<5, 5, 64, kOutDF, 32, kSlices>(a, st);
+            case 80: return launch_tc<5, 5, 80, kOutDF, 32, kSlices>(a, st);
             case 0:
-            case 96: return launch_tc<5, 5, 96, false, 32, kSlices>(a, st);
+            case 96: return launch_tc<5, 5, 96, kOutDF, 32, kSlices>(a, st);
             default: break;
         }
     } else if (tc_bk() == 16) {
         switch (g.bn) {
-            case 64: return launch_tc<kSlices, kGroups, 64, false, 16>(a, st);
-            case 80: return launch_tc<kSlices, kGroups, 80, false, 16>(a, st);
+            case 64: return launch_tc<kSlices, kGroups, 64, kOutDF, 16>(a, st);
+            case 80: return launch_tc<kSlices, kGroups, 80, kOutDF, 16>(a, st);
             case 0:
-            case 96: return launch_tc<kSlices, kGroups, 96, false, 16>(a, st);
+            case 96: return launch_tc<kSlices, kGroups, 96, kOutDF, 16>(a, st);
             default: break;
         }
     } else {
         switch (g.bn) {
-            case 64: return launch_tc<kSlices, kGroups, 64, false, 32>(a, st);
-            case 80: return launch_tc<kSlices, kGroups, 80, false, 32>(a, st);
+            case 64: return launch_tc<kSlices, kGroups, 64, kOutDF, 32>(a, st);
+            case 80: return launch_tc<kSlices, kGroups, 80, kOutDF, 32>(a, st);
             case 0:
-            case 96: return launch_tc<kSlices, kGroups, 96, false, 32>(a, st);
+            case 96: return launch_tc<kSlices, kGroups, 96, kOutDF, 32>(a, st);
             default: break;
         }
     }
@@ -787,16 +874,26 @@ rgf_status oz_gemm_tc(const OzGemm& g, cudaStream_t st) {
     return RGF_E_INVALID;
 }
 
+rgf_status gj_update_tc(int batch, int b, int nbk, const __nv_bfloat16* Ps, const __nv_bfloat16* Ts, float2* C,
+                        long sC, int skip0, int skip1, const int* active, int* status, cudaStream_t st) {
+    // C (b x b, row stride b) += Pbar T: M = b, N = 2b real columns, K =
+    // 2 nbk reals padded to kGjKp; three splits per operand, the six pairs
+    // i + j <= 2 in one FP32 accumulator.  Not counted in the slice-product
+    // GEMM timing (a different product).
+    TcArgs a{batch, b, b, nbk, Ps, Ts, kGjKp, 1.0f, C, sC, 0, C, sC, active, status, TC_WAIT_NS, 0, skip0, skip1};
+    return launch_tc<kGjSplits, 1, 128, kOutC32, 32, kGjSplits>(a, st, false);
+}
+
 rgf_status oz_gemm_hp(const OzGemmHP& g, cudaStream_t st) {
     TcArgs a{g.batch, g.m, g.n, g.k, g.As, g.Bs, g.Kp, g.alpha, g.D, g.sD, g.add_identity, g.C, g.sC, g.active,
              g.status, TC_WAIT_NS, 0};
-    if (g.nsl == 5) return launch_tc<5, 5, 80, true, 32, kSlicesHP>(a, st);
+    if (g.nsl == 5) return launch_tc<5, 5, 80, kOutF64, 32, kSlicesHP>(a, st);
     if (g.nsl != 0 && g.nsl != kSlicesHP) {
         set_error("oz_gemm_hp: unsupported slice count %d", g.nsl);
         return RGF_E_INVALID;
     }
-    if (tc_bk() == 16) return launch_tc<kSlicesHP, kGroupsHP, 80, true, 16>(a, st);
-    return launch_tc<kSlicesHP, kGroupsHP, 80, true, 32>(a, st);
+    if (tc_bk() == 16) return launch_tc<kSlicesHP, kGroupsHP, 80, kOutF64, 16>(a, st);
+    return launch_tc<kSlicesHP, kGroupsHP, 80, kOutF64, 32>(a, st);
 }
 
 }  // namespace rgf

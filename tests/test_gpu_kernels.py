@@ -149,13 +149,81 @@ def test_inverse_flags_singular(rgf):
     assert np.allclose(X[1], np.eye(4))
 
 
-@pytest.mark.parametrize("b", [8, 96, 256])
-def test_inverse_c64(rgf, b):
+def c64_case(b):
     rng = np.random.default_rng(b + 1)
     A = (crand(rng, 2, b, b) + 2.0 * np.eye(b)).astype(np.complex64)
+    if b > 1:
+        A[1, 0, 0] = 0.0  # forces a row interchange
+    return A
+
+
+def c64_residual(A, X):
+    b = A.shape[1]
+    return np.abs(X.astype(np.complex128) @ A.astype(np.complex128) - np.eye(b)).max(axis=(1, 2))
+
+
+# 33, 100: ragged last panel and ragged tensor-core tiles; 320: two full
+# 128-row tiles and a ragged third, five 128-column tiles.
+@pytest.mark.parametrize("b", [8, 33, 96, 100, 256, 320])
+def test_inverse_c64(rgf, b):
+    A = c64_case(b)
     X, flags = rgf.rgf_kernel_inverse_c64(A)
-    r = np.abs(X.astype(np.complex128) @ A.astype(np.complex128) - np.eye(b)).max()
-    assert np.all(flags == 0) and r < 1e-4
+    assert np.all(flags == 0) and c64_residual(A, X).max() < 1e-4
+
+
+def test_inverse_c64_update_cores_agree(rgf, tmp_path):
+    """The seed's trailing updates on the tensor cores (BF16 splits, FP32
+    accumulation) and on the CUDA cores (FP32 FMAs; RGF_GJ_TC=0, read once
+    per process, hence the child process) are both FP32-accurate: the two
+    inverses agree to FP32 rounding times the condition number, and the
+    tensor-core residual is no larger than a small multiple of the other."""
+    import os
+    import subprocess
+    import sys
+    A = c64_case(256)
+    np.save(tmp_path / "A.npy", A)
+    code = (
+        "import numpy as np, sys\n"
+        "from paper_2609_37058_b300 import rgf\n"
+        "d = sys.argv[1]\n"
+        "np.save(d + '/X.npy', rgf.rgf_kernel_inverse_c64(np.load(d + '/A.npy'))[0])\n")
+    env = dict(os.environ, RGF_GJ_TC="0")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    subprocess.run([sys.executable, "-c", code, str(tmp_path)], env=env, cwd=root, check=True, timeout=600)
+    X_cuda = np.load(tmp_path / "X.npy")
+    X_tc, flags = rgf.rgf_kernel_inverse_c64(A)
+    assert np.all(flags == 0)
+    r_tc, r_cuda = c64_residual(A, X_tc), c64_residual(A, X_cuda)
+    assert np.all(r_tc <= 4.0 * r_cuda + 1e-6), (r_tc, r_cuda)
+    cond = np.linalg.cond(A.astype(np.complex128))
+    rel = np.linalg.norm(X_tc - X_cuda, axis=(1, 2)) / np.linalg.norm(X_cuda, axis=(1, 2))
+    assert np.all(rel <= 64 * 6e-8 * cond), (rel, cond)
+
+
+def test_fp64_inverse_from_every_unit_in_one_process(rgf, tmp_path):
+    """The FP64 inverse is launched from several parts of the library (the
+    kernel-level entry, the mixed path's reseeds, the FP64 path), each with
+    its own registration of the panel kernel; at b = 128 the panel needs a
+    raised shared-memory limit, which every one of them must get whichever
+    inverted first (a fresh process, so that the order is this one)."""
+    import os
+    import subprocess
+    import sys
+    code = (
+        "import numpy as np\n"
+        "from paper_2609_37058_b300 import rgf\n"
+        "from synth import make_workload\n"
+        "A = np.eye(128)[None] * 3.0 + np.random.default_rng(0).standard_normal((2, 128, 128))\n"
+        "rgf.rgf_kernel_inverse_f64(A.astype(np.complex128))\n"
+        "dev, E, eta = make_workload('junction_N200_b128')\n"
+        "for prec in (rgf.RGF_MIXED, rgf.RGF_FP64, rgf.RGF_MIXED):\n"
+        "    with rgf.Plan(dev.n_layers, dev.b, precision=prec, eta=eta) as p:\n"
+        "        p.set_device(dev)\n"
+        "        p.transmission(E[:8])\n"
+        "rgf.rgf_kernel_inverse_f64(A.astype(np.complex128))\n")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, PYTHONPATH=os.pathsep.join([root, os.path.join(root, "tests")]))
+    subprocess.run([sys.executable, "-c", code], env=env, cwd=root, check=True, timeout=600)
 
 
 def test_tc_bounded_waits_report_and_recover(rgf):
