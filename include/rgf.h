@@ -89,7 +89,8 @@ typedef enum { RGF_LEAD_LEFT = 0, RGF_LEAD_RIGHT = 1 } rgf_side;
                                     an FP64 seed (in the lead decimation
                                     first by the previous iteration's
                                     inverse), or the last Newton-Schulz step
-                                    left ||I - M X||_F above 3e-7           */
+                                    left ||I - M X||_F above 1e-6 (3e-7 in
+                                    the lead decimation)                    */
 #define RGF_FLAG_LEAD_NEWTON 0x10 /* a lead's surface Green's function kept
                                     its decimation value: the Newton step
                                     that refines it diverged (its Stein

@@ -32,4 +32,14 @@ rgf_status inv_c32(int batch, int b, float2* A, long sA, void* ws, int* flags, c
     return inv_t<float2>(batch, b, A, sA, ws, flags, active, st, nb_override, gj_tc_enabled() ? status : nullptr);
 }
 
+rgf_status inv_c32_to(int batch, int b, float2* A, long sA, void* ws, int* flags, const int* active, int* status,
+                      cudaStream_t st, int nb_override, float4* out_df, double2* out_c128) {
+    if ((out_df != nullptr) == (out_c128 != nullptr)) {
+        set_error("inv_c32_to: exactly one output is required");
+        return RGF_E_INVALID;
+    }
+    return inv_t<float2>(batch, b, A, sA, ws, flags, active, st, nb_override, gj_tc_enabled() ? status : nullptr,
+                         out_df, out_c128);
+}
+
 }  // namespace rgf

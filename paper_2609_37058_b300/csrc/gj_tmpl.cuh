@@ -529,14 +529,58 @@ __global__ void __launch_bounds__(256) k_gj_unpermute(int b, T2* A, long sA, con
     }
 }
 
+// The same column interchanges undone while converting the complex64
+// inverse to the caller's format: out[r][c] = A[r][src[c]] as double-float
+// complex (float4: hi = value, lo = 0) or complex128; A is left as it is.
+// The pivots are staged in shared memory and one thread composes src; a CTA
+// handles 64 rows of one matrix.
+__device__ __forceinline__ void gj_store_as(float4* o, float2 v) { *o = make_float4(v.x, 0.f, v.y, 0.f); }
+__device__ __forceinline__ void gj_store_as(double2* o, float2 v) { *o = make_double2((double)v.x, (double)v.y); }
+constexpr int GJ_UNPERM_ROWS = 64;
+template <typename TO>
+__global__ void __launch_bounds__(256) k_gj_unpermute_to(int b, const float2* __restrict__ A, long sA,
+                                                         const int* __restrict__ piv, TO* __restrict__ out,
+                                                         const int* active) {
+    const int bi = blockIdx.y;
+    if (active && !active[bi]) return;
+    extern __shared__ int gj_perm[];  // src[b], then the pivots[b]
+    int* src = gj_perm;
+    int* pvs = gj_perm + b;
+    const int* pv = piv + (long)bi * b;
+    for (int c = threadIdx.x; c < b; c += blockDim.x) {
+        src[c] = c;
+        pvs[c] = pv[c];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int j = b - 1; j >= 0; --j) {
+            int p = pvs[j];
+            if (!RGF_DCHECK(p >= j && p < b, RGF_DBG_PIVOT)) p = j;
+            const int t = src[j];
+            src[j] = src[p];
+            src[p] = t;
+        }
+    }
+    __syncthreads();
+    const float2* Ab = A + (long)bi * sA;
+    TO* Ob = out + (long)bi * b * b;
+    const int r1 = min(b, (int)(blockIdx.x + 1) * GJ_UNPERM_ROWS);
+    for (int r = blockIdx.x * GJ_UNPERM_ROWS; r < r1; ++r)
+        for (int c = threadIdx.x; c < b; c += blockDim.x) gj_store_as(Ob + (long)r * b + c, Ab[(long)r * b + src[c]]);
+}
+
 // nb_override (16, or 32 where that is the default) replaces the default
 // panel width for b >= 64; 0 keeps it.  The workspace is sized for the
 // default, which is never narrower.
 // tc_status (complex64 only): non-null selects the tensor-core trailing
 // update (gj_update_tc; ws laid out as Pbar splits, T splits, pivots).
+// out_df / out_c128 (complex64 only, at most one non-null): write the
+// inverse there (contiguous b x b per entry) in that format instead of
+// undoing the column interchanges in A.
 template <typename T2>
 rgf_status inv_t(int batch, int b, T2* A, long sA, void* ws, int* flags, const int* active, cudaStream_t st,
-                 int nb_override = 0, int* tc_status = nullptr) {
+                 int nb_override = 0, int* tc_status = nullptr, float4* out_df = nullptr,
+                 double2* out_c128 = nullptr) {
     if (batch <= 0) return RGF_OK;
     int nb = gj_nb(b);
     if (b >= 64 && (nb_override == 16 || (nb_override == 32 && nb == 32))) nb = nb_override;
@@ -607,6 +651,18 @@ rgf_status inv_t(int batch, int b, T2* A, long sA, void* ws, int* flags, const i
             g.skip0 = k0;
             g.skip1 = k0 + nbk;
             RGF_TRY(zgemm_t<T2>(g, st));
+        }
+    }
+    if constexpr (std::is_same<T2, float2>::value) {
+        if (out_df || out_c128) {
+            dim3 g4(ceil_div(b, GJ_UNPERM_ROWS), batch);
+            const size_t smp = 2 * (size_t)b * sizeof(int);
+            if (out_df)
+                k_gj_unpermute_to<float4><<<g4, 256, smp, st>>>(b, A, sA, piv, out_df, active);
+            else
+                k_gj_unpermute_to<double2><<<g4, 256, smp, st>>>(b, A, sA, piv, out_c128, active);
+            RGF_LAUNCH_CHECK();
+            return RGF_OK;
         }
     }
     dim3 g3(ceil_div(b, 32), batch);

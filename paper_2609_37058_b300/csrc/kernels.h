@@ -67,6 +67,11 @@ constexpr int kGjKp = 64;
 size_t inv_c32_workspace_bytes(int batch, int b);
 rgf_status inv_c32(int batch, int b, float2* A, long sA, void* ws, int* flags, const int* active, int* status,
                    cudaStream_t st, int nb_override = 0);
+// The same, with the inverse written to out (contiguous b x b per entry) as
+// double-float complex (hi = the FP32 value, lo = 0) or as complex128,
+// instead of back to A (A keeps the inverse with its columns interchanged).
+rgf_status inv_c32_to(int batch, int b, float2* A, long sA, void* ws, int* flags, const int* active, int* status,
+                      cudaStream_t st, int nb_override, float4* out_df, double2* out_c128);
 // One trailing update: C[:, not in [skip0, skip1)] += Pbar T from the splits
 // (nbk <= 32 columns of Pbar; K padded with zeros to kGjKp).
 rgf_status gj_update_tc(int batch, int b, int nbk, const __nv_bfloat16* Ps, const __nv_bfloat16* Ts, float2* C,

@@ -147,6 +147,13 @@ rgf_status dec_check_dfc(int batch, int b, const float4* alpha, const float4* be
 rgf_status fro_norm_dfc(int batch, int b, const float4* A, double* out, cudaStream_t st);
 rgf_status gamma_dfc(int batch, int b, const float4* sigma, float4* gamma, cudaStream_t st);
 rgf_status axpy_dfc(int batch, int b, float alpha, const float4* X, float4* Y, cudaStream_t st);
+// A double-float inverse is done once |I - M X|_F <= kNsTol: after that
+// step's correction its residual is about |I - M X|_F^2 <= 1e-12.  (3e-7,
+// i.e. 1e-13, moved T by at most 5e-8 on the stored oracle grids at b = 128
+// and 256, against 1e-6 allowed; 1e-6 spares most inverses a third step.)
+// The FP64-class inverses of the lead decimation keep 3e-7.
+constexpr double kNsTol = 1e-6;
+
 // Newton-Schulz bookkeeping for step s of at most max_steps on batch
 // entries i (energy e = i mod W), given R = I - M X:
 //   step 0: theta[i] = 1 / (1 - tr R_i) for a finite residual with
@@ -155,10 +162,10 @@ rgf_status axpy_dfc(int batch, int b, float alpha, const float4* X, float4* Y, c
 //   step 1: entries with |R_i|_F >= 0.5 (or not finite) get bad[i] = 1,
 //     are counted in *bad_count and flagged RGF_FLAG_REFINE; the caller
 //     reseeds them with an FP64 inverse;
-//   next_act[i] = act[i] && |R_i|_F > 3e-7 (after this step's correction
-//     the residual is below |R_i|^2 <= 1e-13, so the entry is done);
+//   next_act[i] = act[i] && |R_i|_F > kNsTol (after this step's correction
+//     the residual is below |R_i|^2 <= 1e-12, so the entry is done);
 //   err[e] = max(err[e], estimated final residual); an entry still above
-//     3e-7 on the last step is flagged RGF_FLAG_REFINE.
+//     kNsTol on the last step is flagged RGF_FLAG_REFINE.
 // more_count (may be null) counts the entries with next_act = 1.
 rgf_status ns_check(int batch, int W, int b, const float4* R, double* err, int* flags, int step, int max_steps,
                     const int* act, int* next_act, int* bad, int* bad_count, double2* theta, cudaStream_t st,

@@ -3,6 +3,7 @@
 // double-float elementwise steps (block formation, decimation updates,
 // broadenings, Newton-Schulz bookkeeping, the FP64 trace reduction).
 #include <atomic>
+#include <cstdlib>
 #include "df.cuh"
 #include "engine.h"
 #include "mixed.h"
@@ -780,7 +781,7 @@ rgf_status axpy_dfc(int batch, int b, float alpha, const float4* X, float4* Y, c
 
 __global__ void k_ns_check(int W, int b, const float4* R, double* err, int* flags, int step, int max_steps,
                            const int* act, int* next_act, int* bad, int* bad_count, double2* theta,
-                           int* more_count) {
+                           int* more_count, double tol) {
     const int bi = blockIdx.x;
     if (act && !act[bi]) {
         if (threadIdx.x == 0) {
@@ -835,7 +836,7 @@ __global__ void k_ns_check(int W, int b, const float4* R, double* err, int* flag
                 atomicOr(flags + e, RGF_FLAG_REFINE);
             }
         }
-        const bool more = !(t <= 3e-7);
+        const bool more = !(t <= tol);
         next_act[bi] = more ? 1 : 0;
         if (more && more_count) atomicAdd(more_count, 1);
         if (more && step == max_steps - 1) atomicOr(flags + e, RGF_FLAG_REFINE);
@@ -855,7 +856,7 @@ rgf_status ns_check(int batch, int W, int b, const float4* R, double* err, int* 
                     int* more_count) {
     if (batch <= 0) return RGF_OK;
     k_ns_check<<<batch, 256, 0, st>>>(W, b, R, err, flags, step, max_steps, act, next_act, bad, bad_count, theta,
-                                      more_count);
+                                      more_count, kNsTol);
     RGF_LAUNCH_CHECK();
     return RGF_OK;
 }

@@ -110,8 +110,7 @@ rgf_status inv_hp(const Ctx& c, int cnt, int W, const double2* M, double2* X, do
                   int* gj_flags, const double2* X_prev) {
     MixedState* m = c.m;
     RGF_TRY(c128_to_c64(cnt, c.b, M, m->c64, act, c.st));
-    RGF_TRY(inv_c32(cnt, c.b, m->c64, c.nn, m->inv_ws, nullptr, act, m->status, c.st));
-    RGF_TRY(c64_to_c128(cnt, c.b, m->c64, X, act, c.st));
+    RGF_TRY(inv_c32_to(cnt, c.b, m->c64, c.nn, m->inv_ws, nullptr, act, m->status, c.st, 0, nullptr, X));
     const int steps = c.ns_steps;
     if (steps == 0) return RGF_OK;
     int* cur = m->nsact[0];
@@ -324,8 +323,7 @@ rgf_status inv_mixed_steps(const Ctx& c, int cnt, int W, const float4* M, float4
         RGF_TRY(dfc_hi_to_c64(cnt, c.b, M, m->c64, act, c.st));
         // An FP32 seed with a zero pivot is not reported: its residual is not
         // finite, so it is reseeded in FP64 below, which reports its own pivots.
-        RGF_TRY(inv_c32(cnt, c.b, m->c64, c.nn, m->inv_ws, nullptr, act, m->status, c.st, m->gj_nb));
-        RGF_TRY(c64_to_dfc(cnt, c.b, m->c64, X, act, c.st));
+        RGF_TRY(inv_c32_to(cnt, c.b, m->c64, c.nn, m->inv_ws, nullptr, act, m->status, c.st, m->gj_nb, X, nullptr));
         if (steps == 0) return RGF_OK;
         RGF_TRY(mask_init(cnt, act, m->nsact[0], c.st));
         RGF_TRY(sliceA(c, cnt, 1, M, act));
