@@ -93,6 +93,70 @@ __device__ __forceinline__ float4 zsh_df(float2 zr, float2 zi, float4 sv, float4
 }
 __device__ __forceinline__ float4 conj_df(float4 v) { return make_float4(v.x, v.y, -v.z, -v.w); }
 
+// Slices of the formed element v (row r, column j) in the A layout, and of
+// the element at row i of column c in the B layout of the K-interleaved
+// product (rows 2c: (Re, -Im), 2c + 1: (Im, Re)).
+__device__ __forceinline__ void put_row_slices(__nv_bfloat16* out, int bi, int b, int r, int Kp, int j, float4 v,
+                                               int e) {
+    float sr[kSlices], si[kSlices];
+    slice6(v.x, v.y, e, sr);
+    slice6(v.z, v.w, e, si);
+#pragma unroll
+    for (int s = 0; s < kSlices; ++s) {
+        __nv_bfloat162 p;
+        p.x = __float2bfloat16_rn(sr[s]);
+        p.y = __float2bfloat16_rn(si[s]);
+        *reinterpret_cast<__nv_bfloat162*>(out + (((long)bi * kSlices + s) * b + r) * Kp + 2 * j) = p;
+    }
+}
+__device__ __forceinline__ void put_col_slices(__nv_bfloat16* out, int bi, int b, int c, int Kp, int i, float4 v,
+                                               int e) {
+    float sr[kSlices], si[kSlices];
+    slice6(v.x, v.y, e, sr);
+    slice6(v.z, v.w, e, si);
+    const long rows = 2L * b;
+#pragma unroll
+    for (int s = 0; s < kSlices; ++s) {
+        __nv_bfloat16* base = out + (((long)bi * kSlices + s) * rows) * Kp;
+        __nv_bfloat162 p0, p1;
+        p0.x = __float2bfloat16_rn(sr[s]);
+        p0.y = __float2bfloat16_rn(-si[s]);
+        p1.x = __float2bfloat16_rn(si[s]);
+        p1.y = __float2bfloat16_rn(sr[s]);
+        *reinterpret_cast<__nv_bfloat162*>(base + (2L * c) * Kp + 2 * i) = p0;
+        *reinterpret_cast<__nv_bfloat162*>(base + (2L * c + 1) * Kp + 2 * i) = p1;
+    }
+}
+
+// One warp forms the b elements of a row (or column) with form(i), finds
+// their largest |Re|, |Im| for the slice exponent and writes the slices with
+// put(i, v, e).  The first 32 * kFormCache elements stay in registers between
+// the two passes (all of them for b <= 256); the rest are formed again.
+constexpr int kFormCache = 8;
+template <typename Form, typename Put>
+__device__ __forceinline__ void form_slice_warp(int b, int lane, Form form, Put put) {
+    float4 cache[kFormCache];
+    float mx = 0.0f;
+#pragma unroll
+    for (int t = 0; t < kFormCache; ++t) {
+        const int i = lane + 32 * t;
+        cache[t] = i < b ? form(i) : make_float4(0.f, 0.f, 0.f, 0.f);
+        mx = fmaxf(mx, fmaxf(fabsf(cache[t].x), fabsf(cache[t].z)));
+    }
+    for (int i = lane + 32 * kFormCache; i < b; i += 32) {
+        const float4 v = form(i);
+        mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.z)));
+    }
+    mx = warp_max(mx);
+    const int e = exp_above(mx);
+#pragma unroll
+    for (int t = 0; t < kFormCache; ++t) {
+        const int i = lane + 32 * t;
+        if (i < b) put(i, cache[t], e);
+    }
+    for (int i = lane + 32 * kFormCache; i < b; i += 32) put(i, form(i), e);
+}
+
 // A-operand slices of tau = z S - H (one warp per row, one batch entry per
 // energy; S, H shared b x b df blocks): the formed matrix never goes to
 // memory.  Same layout as k_slice_rows.
@@ -106,26 +170,9 @@ __global__ void __launch_bounds__(256) k_form_slice_rows(int b, const double* __
     const float2 zr = df_from_double(E[bi]), zi = df_from_double(eta);
     const float4* Sr = S + (long)r * b;
     const float4* Hr = H + (long)r * b;
-    float mx = 0.0f;
-    for (int j = lane; j < b; j += 32) {
-        const float4 v = zsh_df(zr, zi, Sr[j], Hr[j]);
-        mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.z)));
-    }
-    mx = warp_max(mx);
-    const int e = exp_above(mx);
-    for (int j = lane; j < b; j += 32) {
-        const float4 v = zsh_df(zr, zi, Sr[j], Hr[j]);
-        float sr[kSlices], si[kSlices];
-        slice6(v.x, v.y, e, sr);
-        slice6(v.z, v.w, e, si);
-#pragma unroll
-        for (int s = 0; s < kSlices; ++s) {
-            __nv_bfloat162 p;
-            p.x = __float2bfloat16_rn(sr[s]);
-            p.y = __float2bfloat16_rn(si[s]);
-            *reinterpret_cast<__nv_bfloat162*>(out + (((long)bi * kSlices + s) * b + r) * Kp + 2 * j) = p;
-        }
-    }
+    form_slice_warp(
+        b, lane, [&](int j) { return zsh_df(zr, zi, Sr[j], Hr[j]); },
+        [&](int j, float4 v, int e) { put_row_slices(out, bi, b, r, Kp, j, v, e); });
 }
 
 // B-operand slices of tau' = z S^dagger - H^dagger (one warp per column c of
@@ -142,31 +189,9 @@ __global__ void __launch_bounds__(256) k_form_slice_cols_dag(int b, const double
     const float2 zr = df_from_double(E[bi]), zi = df_from_double(eta);
     const float4* Sc = S + (long)c * b;
     const float4* Hc = H + (long)c * b;
-    float mx = 0.0f;
-    for (int i = lane; i < b; i += 32) {
-        const float4 v = zsh_df(zr, zi, conj_df(Sc[i]), conj_df(Hc[i]));
-        mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.z)));
-    }
-    mx = warp_max(mx);
-    const int e = exp_above(mx);
-    const long rows = 2L * b;
-    for (int i = lane; i < b; i += 32) {
-        const float4 v = zsh_df(zr, zi, conj_df(Sc[i]), conj_df(Hc[i]));
-        float sr[kSlices], si[kSlices];
-        slice6(v.x, v.y, e, sr);
-        slice6(v.z, v.w, e, si);
-#pragma unroll
-        for (int s = 0; s < kSlices; ++s) {
-            __nv_bfloat16* base = out + (((long)bi * kSlices + s) * rows) * Kp;
-            __nv_bfloat162 p0, p1;
-            p0.x = __float2bfloat16_rn(sr[s]);
-            p0.y = __float2bfloat16_rn(-si[s]);
-            p1.x = __float2bfloat16_rn(si[s]);
-            p1.y = __float2bfloat16_rn(sr[s]);
-            *reinterpret_cast<__nv_bfloat162*>(base + (2L * c) * Kp + 2 * i) = p0;
-            *reinterpret_cast<__nv_bfloat162*>(base + (2L * c + 1) * Kp + 2 * i) = p1;
-        }
-    }
+    form_slice_warp(
+        b, lane, [&](int i) { return zsh_df(zr, zi, conj_df(Sc[i]), conj_df(Hc[i])); },
+        [&](int i, float4 v, int e) { put_col_slices(out, bi, b, c, Kp, i, v, e); });
 }
 
 // Table-driven forms of the two kernels above for the server's energy
@@ -184,26 +209,9 @@ __global__ void __launch_bounds__(256) k_form_slice_rows_tab(int b, const SlotTa
     const float2 zr = df_from_double(t.E), zi = df_from_double(t.eta);
     const float4* Sr = t.Sl + (long)r * b;
     const float4* Hr = t.Hl + (long)r * b;
-    float mx = 0.0f;
-    for (int j = lane; j < b; j += 32) {
-        const float4 v = zsh_df(zr, zi, Sr[j], Hr[j]);
-        mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.z)));
-    }
-    mx = warp_max(mx);
-    const int e = exp_above(mx);
-    for (int j = lane; j < b; j += 32) {
-        const float4 v = zsh_df(zr, zi, Sr[j], Hr[j]);
-        float sr[kSlices], si[kSlices];
-        slice6(v.x, v.y, e, sr);
-        slice6(v.z, v.w, e, si);
-#pragma unroll
-        for (int s = 0; s < kSlices; ++s) {
-            __nv_bfloat162 p;
-            p.x = __float2bfloat16_rn(sr[s]);
-            p.y = __float2bfloat16_rn(si[s]);
-            *reinterpret_cast<__nv_bfloat162*>(out + (((long)bi * kSlices + s) * b + r) * Kp + 2 * j) = p;
-        }
-    }
+    form_slice_warp(
+        b, lane, [&](int j) { return zsh_df(zr, zi, Sr[j], Hr[j]); },
+        [&](int j, float4 v, int e) { put_row_slices(out, bi, b, r, Kp, j, v, e); });
 }
 
 __global__ void __launch_bounds__(256) k_form_slice_cols_dag_tab(int b, const SlotTab* __restrict__ tab,
@@ -218,31 +226,9 @@ __global__ void __launch_bounds__(256) k_form_slice_cols_dag_tab(int b, const Sl
     const float2 zr = df_from_double(t.E), zi = df_from_double(t.eta);
     const float4* Sc = t.Sl + (long)c * b;
     const float4* Hc = t.Hl + (long)c * b;
-    float mx = 0.0f;
-    for (int i = lane; i < b; i += 32) {
-        const float4 v = zsh_df(zr, zi, conj_df(Sc[i]), conj_df(Hc[i]));
-        mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.z)));
-    }
-    mx = warp_max(mx);
-    const int e = exp_above(mx);
-    const long rows = 2L * b;
-    for (int i = lane; i < b; i += 32) {
-        const float4 v = zsh_df(zr, zi, conj_df(Sc[i]), conj_df(Hc[i]));
-        float sr[kSlices], si[kSlices];
-        slice6(v.x, v.y, e, sr);
-        slice6(v.z, v.w, e, si);
-#pragma unroll
-        for (int s = 0; s < kSlices; ++s) {
-            __nv_bfloat16* base = out + (((long)bi * kSlices + s) * rows) * Kp;
-            __nv_bfloat162 p0, p1;
-            p0.x = __float2bfloat16_rn(sr[s]);
-            p0.y = __float2bfloat16_rn(-si[s]);
-            p1.x = __float2bfloat16_rn(si[s]);
-            p1.y = __float2bfloat16_rn(sr[s]);
-            *reinterpret_cast<__nv_bfloat162*>(base + (2L * c) * Kp + 2 * i) = p0;
-            *reinterpret_cast<__nv_bfloat162*>(base + (2L * c + 1) * Kp + 2 * i) = p1;
-        }
-    }
+    form_slice_warp(
+        b, lane, [&](int i) { return zsh_df(zr, zi, conj_df(Sc[i]), conj_df(Hc[i])); },
+        [&](int i, float4 v, int e) { put_col_slices(out, bi, b, c, Kp, i, v, e); });
 }
 
 rgf_status form_slice_rows_tab(int S, int b, const SlotTab* tab, const int* mask, __nv_bfloat16* out, int Kp,

@@ -707,6 +707,287 @@ __global__ void __launch_bounds__(320, 1)
     }
 }
 
+// ---------------------------------------------------------------- CTA pair
+// Two-SM form for row tiles of 256 (M = 256 per MMA, tcgen05 cta_group::2):
+// a cluster of two CTAs computes a 256 x BN tile.  Each CTA stages its own
+// 128 rows of the A slices and half (BN / 2 rows) of the B slices; the
+// leader CTA (cluster rank 0) issues the MMAs, which read both CTAs' tiles,
+// and each CTA's TMEM receives its 128 rows of the BN accumulator columns.
+// Per SM this halves the B operand's shared-memory reads (A 4 KB + B 1.5 KB
+// per 128 x BN x 16 MMA instead of 4 + 3 KB) and halves the stage, so three
+// stages fit.  Synchronisation: the peer's TMA copies complete on the
+// leader's full barrier (which the leader's producer arms for both CTAs'
+// bytes); the leader's commits arrive on the empty and accumulator-full
+// barriers of both CTAs (multicast); both CTAs' epilogue warps release the
+// accumulators on the leader's accumulator-empty barrier.  Every wait is
+// bounded as in the one-SM form; both CTAs meet at a cluster barrier before
+// the TMEM is released.
+template <int NSL, int NGRP, int BN>
+struct TcCfg2 {
+    static constexpr int BK = 32, STAGES = 3;
+    static constexpr int ATILE = TC_BM * BK * 2;     // this CTA's 128 rows of one A slice
+    static constexpr int BTILE = (BN / 2) * BK * 2;  // this CTA's BN / 2 rows of one B slice
+    static constexpr int STAGE = NSL * (ATILE + BTILE);
+    static constexpr int SMEM = STAGES * STAGE + 1024 + 256;
+    // D = F32, A = B = BF16, K-major, N = BN, M = 256 (the pair).
+    static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                                      ((uint32_t)(256 >> 4) << 24);
+    static constexpr uint64_t SWZ = 4;
+    static constexpr uint32_t SBO = 8 * BK * 2;
+    static_assert(NGRP * BN <= 512, "accumulators exceed TMEM");
+    static_assert(BTILE % 1024 == 0, "B half tiles must keep swizzle-atom alignment");
+    static_assert(SMEM <= 227 * 1024, "stages exceed shared memory");
+};
+
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cluster_id_x() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cluster_count_x() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+    return r;
+}
+// Shared::cluster address of the object at this CTA's shared address a in
+// the CTA of the given cluster rank.
+__device__ __forceinline__ uint32_t mapa_rank(uint32_t a, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t cluster_addr) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+// TMA load into this CTA's shared memory whose completion is signalled on
+// the mbarrier at a shared::cluster address (the leader's for both CTAs).
+__device__ __forceinline__ void tma_load_3d_pair(uint32_t dst, const CUtensorMap* map, int x, int y, int z,
+                                                 uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
+        "%3, %4}], [%5];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void umma_pair(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(accum));
+}
+// Completion of the leader's MMAs arrives on the barrier at this shared
+// offset in both CTAs of the pair.
+__device__ __forceinline__ void umma_pair_commit(uint32_t bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
+        "h"((unsigned short)0x3)
+        : "memory");
+}
+
+template <int NSL, int NGRP, int BN>
+__device__ __forceinline__ void mma_chunk_pair(const unsigned char* st, uint32_t taddr, bool first) {
+    using Cfg = TcCfg2<NSL, NGRP, BN>;
+    const uint64_t da = desc_sw(smem_u32(st), Cfg::SWZ, Cfg::SBO);
+    const uint64_t db = desc_sw(smem_u32(st + NSL * Cfg::ATILE), Cfg::SWZ, Cfg::SBO);
+    uint32_t started = 0;
+#pragma unroll
+    for (int i = 0; i < NSL; ++i) {
+#pragma unroll
+        for (int j = 0; j < NSL; ++j) {
+            if (i + j > NSL - 1) continue;
+            const int grp = (i + j) < (NGRP - 1) ? (i + j) : (NGRP - 1);
+#pragma unroll
+            for (int kk = 0; kk < Cfg::BK / 16; ++kk) {
+                const uint64_t ad = da + (uint64_t)((i * Cfg::ATILE + kk * 32) >> 4);
+                const uint64_t bd = db + (uint64_t)((j * Cfg::BTILE + kk * 32) >> 4);
+                const uint32_t acc = (!first || (started >> grp) & 1u) ? 1u : 0u;
+                umma_pair(taddr + (uint32_t)(grp * BN), ad, bd, Cfg::IDESC, acc);
+                started |= 1u << grp;
+            }
+        }
+    }
+}
+
+template <int NSL, int NGRP, int BN, int PL>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(320, 1)
+    k_oz_tc_pair(TcArgs g, const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB) {
+    using Cfg = TcCfg2<NSL, NGRP, BN>;
+    constexpr int S = Cfg::STAGES;
+    constexpr int NQ = BN / 16;
+    constexpr int NCH = (NQ + 1) / 2;
+    static_assert(BN == 64 || BN == 96, "the deferred epilogue holds the chunks of a 64 or 96 wide tile");
+    extern __shared__ __align__(1024) unsigned char smem_tc[];
+    unsigned char* base = (unsigned char*)(((uintptr_t)smem_tc + 1023) & ~(uintptr_t)1023);
+    // bars[0..S-1] full, bars[S..2S-1] empty, bars[2S] accumulators full,
+    // bars[2S+1] accumulators empty (the leader's counts both CTAs' warps).
+    uint64_t* bars = reinterpret_cast<uint64_t*>(base + S * Cfg::STAGE);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * S + 2);
+    volatile int* s_fail = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    volatile int* s_issued = s_fail + 1;
+    volatile int* s_consumed = s_fail + 2;
+    const uint32_t acc_full = smem_u32(&bars[2 * S]), acc_empty = smem_u32(&bars[2 * S + 1]);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t rank = cluster_ctarank();
+    const bool leader = rank == 0;
+    const int cl = (int)cluster_id_x(), ncl = (int)cluster_count_x();
+    const int ntx = (2 * g.n + BN - 1) / BN, nty = (g.m + 255) / 256;
+    const int ntiles = ntx * nty * g.batch;
+    const int nk = g.Kp / Cfg::BK;
+    int* status = g.status;
+
+    if (tid == 0) {
+        for (int i = 0; i < 2 * S + 1; ++i) mbar_init(smem_u32(&bars[i]), 1);
+        mbar_init(acc_empty, 16);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        *s_fail = 0;
+        *s_issued = 0;
+        *s_consumed = 0;
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(TC_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    // Both CTAs' barriers are initialised and their TMEM allocated before
+    // either signals the other.
+    cluster_sync_all();
+    tc_fence_after();
+    const uint32_t taddr = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- TMA producer (both CTAs)
+            int gc = 0;
+            for (int t = cl; t < ntiles && !*s_fail; t += ncl) {
+                const int bx = t % ntx, by = (t / ntx) % nty, bi = t / (ntx * nty);
+                if (g.active && !g.active[bi]) continue;
+                bool ok = true;
+                for (int kc = 0; kc < nk; ++kc, ++gc) {
+                    const int s = gc % S;
+                    if (gc >= S && !mbar_wait(smem_u32(&bars[S + s]), ((gc / S) - 1) & 1, status, 0x1, g.wait_ns)) {
+                        ok = false;
+                        break;
+                    }
+                    *s_issued = gc + 1;
+                    const uint32_t fb_local = smem_u32(&bars[s]);
+                    if (leader) mbar_expect_tx(fb_local, 2 * Cfg::STAGE);
+                    const uint32_t fb = mapa_rank(fb_local, 0);
+                    unsigned char* st = base + s * Cfg::STAGE;
+#pragma unroll
+                    for (int sl = 0; sl < NSL; ++sl) {
+                        tma_load_3d_pair(smem_u32(st + sl * Cfg::ATILE), &tmA, kc * Cfg::BK, by * 256 + (int)rank * TC_BM,
+                                         bi * PL + sl, fb);
+                        tma_load_3d_pair(smem_u32(st + NSL * Cfg::ATILE + sl * Cfg::BTILE), &tmB, kc * Cfg::BK,
+                                         bx * BN + (int)rank * (BN / 2), bi * PL + sl, fb);
+                    }
+                }
+                if (!ok) {
+                    *s_fail = 1;
+                    break;
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0 && leader) {
+            // ---------------- MMA issuer (leader CTA)
+            int gc = 0, lt = 0;
+            for (int t = cl; t < ntiles && !*s_fail; t += ncl) {
+                const int bi = t / (ntx * nty);
+                if (g.active && !g.active[bi]) continue;
+                if (lt > 0 && !mbar_wait(acc_empty, (lt - 1) & 1, status, 0x2, g.wait_ns)) {
+                    *s_fail = 1;
+                    break;
+                }
+                tc_fence_after();
+                bool ok = true;
+                for (int kc = 0; kc < nk; ++kc, ++gc) {
+                    const int s = gc % S;
+                    if (!mbar_wait(smem_u32(&bars[s]), (gc / S) & 1, status, 0x2, g.wait_ns)) {
+                        ok = false;
+                        break;
+                    }
+                    *s_consumed = gc + 1;
+                    tc_fence_after();
+                    mma_chunk_pair<NSL, NGRP, BN>(base + s * Cfg::STAGE, taddr, kc == 0);
+                    umma_pair_commit(smem_u32(&bars[S + s]));
+                }
+                if (!ok) *s_fail = 1;
+                // Committed also after a failure, so that the epilogues' waits end.
+                umma_pair_commit(acc_full);
+                if (!ok) break;
+                ++lt;
+            }
+        }
+    } else {
+        // ---------------- epilogue (both CTAs): this CTA's 128 rows
+        const int quad = warp & 3;
+        const int half = (warp - 2) >> 2;
+        const uint32_t trow = taddr + ((uint32_t)(quad * 32) << 16);
+        const uint32_t release = mapa_rank(acc_empty, 0);
+        int lt = 0;
+        for (int t = cl; t < ntiles; t += ncl) {
+            const int bx = t % ntx, by = (t / ntx) % nty, bi = t / (ntx * nty);
+            if (g.active && !g.active[bi]) continue;
+            int ok_i = 0;
+            if (lane == 0) ok_i = (mbar_wait(acc_full, lt & 1, status, 0x4, g.wait_ns) && !*s_fail) ? 1 : 0;
+            if (__shfl_sync(0xffffffffu, ok_i, 0) == 0) break;
+            tc_fence_after();
+            const int r = by * 256 + (int)rank * TC_BM + quad * 32 + lane;
+            float4 res[NCH][8];
+#pragma unroll
+            for (int k = 0; k < NCH; ++k) {
+                const int q = half + 2 * k;
+                if (q < NQ) {
+                    float v[NGRP][16];
+#pragma unroll
+                    for (int gq = 0; gq < NGRP; ++gq) tmem_ld16(trow + gq * BN + q * 16, v[gq]);
+                    tmem_ld_wait();
+                    if (q + 2 >= NQ) {
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive_remote(release);
+                    }
+                    combine_chunk<NGRP, kOutDF>(g, v, res[k]);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < NCH; ++k) {
+                const int q = half + 2 * k;
+                if (q < NQ) finish_chunk<kOutDF>(g, res[k], bi, r, (bx * BN + q * 16) >> 1);
+            }
+            ++lt;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0 && leader && *s_fail) {
+        // Copies issued but not received by the MMA issuer complete on the
+        // leader's full barriers (both CTAs' bytes).
+        for (int c = *s_consumed; c < *s_issued; ++c)
+            mbar_wait(smem_u32(&bars[c % S]), (c / S) & 1, status, 0x8, g.wait_ns);
+    }
+    __syncthreads();
+    // Neither CTA releases its TMEM or exits while its peer may still
+    // signal its barriers or read its tiles.
+    cluster_sync_all();
+    if (warp == 1) {
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(TC_TMEM_COLS)
+                     : "memory");
+    }
+}
+
 // The driver's tensor-map encoder, looked up at run time so that the library
 // loads (and its host-only entry points work) on machines without a driver.
 static PFN_cuTensorMapEncodeTiled_v12000 encoder() {
@@ -816,6 +1097,75 @@ static rgf_status launch_tc(const TcArgs& g, cudaStream_t st, bool count_work = 
     return RGF_OK;
 }
 
+// Two-SM tiles for row counts that are multiples of 256 with RGF_TC_PAIR=1
+// in the environment (read once).  Off by default: at b = 256 (296 entries)
+// the pair took 711 us per product against 693 us for the one-SM kernel,
+// both with the tensor pipe about 60% active, so neither the B operand's
+// shared-memory reads nor the stage depth is what limits this GEMM.
+static bool tc_pair_enabled() {
+    static const bool on = [] {
+        const char* e = getenv("RGF_TC_PAIR");
+        return e && e[0] == '1';
+    }();
+    return on;
+}
+
+template <int NSL, int NGRP, int BN, int PL>
+static rgf_status launch_tc_pair(const TcArgs& g, cudaStream_t st) {
+    using Cfg = TcCfg2<NSL, NGRP, BN>;
+    if (g.batch <= 0) return RGF_OK;
+    if (g.Kp % Cfg::BK != 0 || ((uintptr_t)g.As & 15) || ((uintptr_t)g.Bs & 15) || !g.status || g.m % 256 != 0) {
+        set_error("oz_gemm_tc (pair): bad slice layout");
+        return RGF_E_INVALID;
+    }
+    if ((long)g.batch * PL > 0x7fffffffL) {
+        set_error("oz_gemm_tc (pair): batch too large");
+        return RGF_E_INVALID;
+    }
+    CUtensorMap ta, tb;
+    RGF_TRY(encode_slices(&ta, g.As, g.Kp, g.m, (long)g.batch * PL, TC_BM, Cfg::BK));
+    RGF_TRY(encode_slices(&tb, g.Bs, g.Kp, 2L * g.n, (long)g.batch * PL, BN / 2, Cfg::BK));
+    // Resident clusters of this kernel (one CTA per SM), found once.
+    static std::atomic<int> max_clusters{0};
+    if (max_clusters.load() == 0) {
+        RGF_CUDA_TRY(cudaFuncSetAttribute(k_oz_tc_pair<NSL, NGRP, BN, PL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          Cfg::SMEM));
+        int dev = 0, nsm = 0;
+        RGF_CUDA_TRY(cudaGetDevice(&dev));
+        RGF_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(nsm & ~1), 1, 1);
+        cfg.blockDim = dim3(320, 1, 1);
+        cfg.dynamicSmemBytes = Cfg::SMEM;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 2;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int n = 0;
+        RGF_CUDA_TRY(cudaOccupancyMaxActiveClusters(&n, (const void*)k_oz_tc_pair<NSL, NGRP, BN, PL>, &cfg));
+        if (n < 1) {
+            set_error("oz_gemm_tc (pair): no CTA pair of %d bytes of shared memory fits", Cfg::SMEM);
+            return RGF_E_CUDA;
+        }
+        max_clusters.store(n);
+    }
+    const long ntiles = (long)ceil_div(2L * g.n, BN) * (g.m / 256) * g.batch;
+    const int ncl = (int)(ntiles < max_clusters.load() ? ntiles : max_clusters.load());
+    const bool timed = gemm_timing_enabled() && g.active == nullptr;
+    cudaEvent_t ev = nullptr;
+    if (timed) gemm_timing_before(st, &ev);
+    k_oz_tc_pair<NSL, NGRP, BN, PL><<<2 * ncl, 320, Cfg::SMEM, st>>>(g, ta, tb);
+    RGF_LAUNCH_CHECK();
+    if (timed) {
+        const double pairs = (double)(NSL * (NSL + 1) / 2);
+        gemm_timing_after(st, ev, pairs * 2.0 * g.m * (2.0 * g.n) * (2.0 * g.k) * g.batch);
+    }
+    return RGF_OK;
+}
+
 // K per pipeline stage of the tensor-core cores: 32 (default) or 16 with
 // RGF_TC_BK=16 in the environment (read once).
 static int tc_bk() {
@@ -832,6 +1182,11 @@ rgf_status oz_gemm_tc(const OzGemm& g, cudaStream_t st) {
     if (g.test_wait_ns) {
         a.wait_ns = g.test_wait_ns;
         a.skip_first_chunk = 1;
+    }
+    if (g.m % 256 == 0 && !g.test_wait_ns && tc_persistent() && tc_pair_enabled() && tc_bk() == 32 &&
+        (g.bn == 0 || g.bn == 96)) {
+        if (g.nsl == 4) return launch_tc_pair<4, 4, 96, kSlices>(a, st);
+        if (g.nsl == 0 || g.nsl == kSlices) return launch_tc_pair<kSlices, kGroups, 96, kSlices>(a, st);
     }
     if (g.nsl == 4) {
         // Four of the six slices (ten pairs, four exact groups): for

@@ -200,6 +200,37 @@ def test_inverse_c64_update_cores_agree(rgf, tmp_path):
     assert np.all(rel <= 64 * 6e-8 * cond), (rel, cond)
 
 
+def test_pair_and_single_sm_gemms_agree(rgf, tmp_path):
+    """The two-SM form of the slice-product GEMM (tcgen05 cta_group::2 on a
+    cluster of two CTAs, 256-row tiles; RGF_TC_PAIR=1, read once per
+    process, hence the child process) issues the same products into the
+    same accumulators as the one-SM kernel: bit-identical results, including
+    ragged N and K and two row tiles."""
+    import os
+    import subprocess
+    import sys
+    rng = np.random.default_rng(31)
+    cases = [(3, 256, 256, 256), (2, 256, 200, 136), (2, 512, 96, 64)]
+    for i, (batch, m, n, k) in enumerate(cases):
+        np.save(tmp_path / f"A{i}.npy", crand(rng, batch, m, k))
+        np.save(tmp_path / f"B{i}.npy", crand(rng, batch, k, n))
+    code = (
+        "import numpy as np, sys\n"
+        "from paper_2609_37058_b300 import rgf\n"
+        "d = sys.argv[1]\n"
+        f"for i in range({len(cases)}):\n"
+        "    A, B = np.load(f'{d}/A{i}.npy'), np.load(f'{d}/B{i}.npy')\n"
+        "    np.save(f'{d}/C{i}.npy', rgf.rgf_kernel_zgemm_mixed(A, B, core=0))\n")
+    env = dict(os.environ, RGF_TC_PAIR="1")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    subprocess.run([sys.executable, "-c", code, str(tmp_path)], env=env, cwd=root, check=True, timeout=600)
+    for i in range(len(cases)):
+        A, B = np.load(tmp_path / f"A{i}.npy"), np.load(tmp_path / f"B{i}.npy")
+        C_pair = np.load(tmp_path / f"C{i}.npy")
+        assert np.array_equal(rgf.rgf_kernel_zgemm_mixed(A, B, core=0), C_pair), cases[i]
+        assert np.all(np.abs(C_pair - A @ B) <= mixed_bound(A, B)), cases[i]
+
+
 def test_fp64_inverse_from_every_unit_in_one_process(rgf, tmp_path):
     """The FP64 inverse is launched from several parts of the library (the
     kernel-level entry, the mixed path's reseeds, the FP64 path), each with
