@@ -71,6 +71,7 @@ struct OzGemm {
     const float4* D; long sD;    // optional addend (may alias C)
     int add_identity;            // C += I
     float4* C; long sC;
+    float2* C2;                  // optional: C rounded to complex64 as well (same layout)
     const int* active;
     int* status;                 // device word, nonzero after a pipeline timeout
     // Test hook (0 in normal use): nonzero makes the tcgen05 core skip the

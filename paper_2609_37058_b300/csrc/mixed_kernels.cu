@@ -550,34 +550,38 @@ __global__ void k_form_dfc(int W, int b, const double* __restrict__ E, double et
     const long nn = (long)b * b;
     float4* o = out + (long)be * nn;
     const float4* sb = sub ? sub + (long)be * nn : nullptr;
-    for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < nn; idx += (long)gridDim.x * blockDim.x) {
-        const int r = (int)(idx / b), c = (int)(idx % b);
-        const long si = tr ? (long)c * b + r : idx;
-        float4 sv = S ? S[si] : make_float4(0.f, 0.f, 0.f, 0.f);
-        float4 hv = H[si];
-        if (tr) {
-            sv.z = -sv.z;
-            sv.w = -sv.w;
-            hv.z = -hv.z;
-            hv.w = -hv.w;
+    // One warp per row, lanes along the columns (no index division).
+    const int warps = blockDim.x >> 5, lane = threadIdx.x & 31;
+    for (int r = blockIdx.x * warps + (threadIdx.x >> 5); r < b; r += gridDim.x * warps) {
+        for (int c = lane; c < b; c += 32) {
+            const long idx = (long)r * b + c;
+            const long si = tr ? (long)c * b + r : idx;
+            float4 sv = S ? S[si] : make_float4(0.f, 0.f, 0.f, 0.f);
+            float4 hv = H[si];
+            if (tr) {
+                sv.z = -sv.z;
+                sv.w = -sv.w;
+                hv.z = -hv.z;
+                hv.w = -hv.w;
+            }
+            // (zr + i zi)(Sr + i Si) - (Hr + i Hi)
+            const float2 sr = re_of(sv), sim = im_of(sv);
+            float2 re = df_sub(df_sub(df_mul(zr, sr), df_mul(zi, sim)), re_of(hv));
+            float2 im = df_sub(df_add(df_mul(zr, sim), df_mul(zi, sr)), im_of(hv));
+            if (sb) {
+                const float4 d = sb[idx];
+                re = df_sub(re, re_of(d));
+                im = df_sub(im, im_of(d));
+            }
+            o[idx] = cdf(re, im);
         }
-        // (zr + i zi)(Sr + i Si) - (Hr + i Hi)
-        const float2 sr = re_of(sv), sim = im_of(sv);
-        float2 re = df_sub(df_sub(df_mul(zr, sr), df_mul(zi, sim)), re_of(hv));
-        float2 im = df_sub(df_add(df_mul(zr, sim), df_mul(zi, sr)), im_of(hv));
-        if (sb) {
-            const float4 d = sb[idx];
-            re = df_sub(re, re_of(d));
-            im = df_sub(im, im_of(d));
-        }
-        o[idx] = cdf(re, im);
     }
 }
 
 rgf_status form_dfc(int W, int nsrc, int b, const double* E, double eta, const FormSrcDf& src, float4* out,
                     const float4* sub, const int* active, cudaStream_t st) {
     if (W <= 0) return RGF_OK;
-    k_form_dfc<<<dim3(grid_for2((long)b * b, 256, 64), W * nsrc), 256, 0, st>>>(W, b, E, eta, src, out, sub,
+    k_form_dfc<<<dim3(ceil_div(b, 8), W * nsrc), 256, 0, st>>>(W, b, E, eta, src, out, sub,
                                                                                   active);
     RGF_LAUNCH_CHECK();
     return RGF_OK;

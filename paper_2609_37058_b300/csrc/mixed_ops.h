@@ -94,7 +94,7 @@ struct Ctx {
 rgf_status sliceA(const Ctx& c, int cnt, int ia, const float4* A, const int* act, int planes = kSlices);
 rgf_status sliceB(const Ctx& c, int cnt, int ib, const float4* B, const int* act, int planes = kSlices);
 rgf_status mm(const Ctx& c, int cnt, int ia, int ib, float alpha, const float4* D, int addI, float4* C,
-              const int* act);
+              const int* act, float2* C2 = nullptr);
 // C = A B + D from the four most significant slices of each operand.
 rgf_status mm4(const Ctx& c, int cnt, int ia, int ib, const float4* D, float4* C, const int* act);
 // Seven-slice (FP64-class) counterparts for FP64 matrices.
@@ -107,13 +107,15 @@ rgf_status hmm(const Ctx& c, int cnt, int ia, int ib, float alpha, const double2
 // X = M^-1 (df) for cnt entries: FP32 seed, Newton-Schulz refinement with a
 // Sherman-Morrison-scaled first step, FP64 reseed of entries that do not
 // contract.  R is df scratch of cnt matrices.
+// m64_ready: MixedState::c64 already holds M rounded to complex64 (written
+// by the GEMM that produced M).
 rgf_status inv_mixed(const Ctx& c, int cnt, int W, const float4* M, float4* X, float4* R, const int* act,
-                     int* gj_flags);
+                     int* gj_flags, bool m64_ready = false);
 // The same in parts: the seed (when s_begin == 0) and Newton-Schulz steps
 // s_begin .. s_end-1.  From step 1 on, MixedState::more_count holds the
 // number of entries that need another step.
 rgf_status inv_mixed_steps(const Ctx& c, int cnt, int W, const float4* M, float4* X, float4* R, const int* act,
-                           int* gj_flags, int s_begin, int s_end);
+                           int* gj_flags, int s_begin, int s_end, bool m64_ready = false);
 // The same for FP64 matrices with seven-slice products.
 // X_prev (optional): inverses of nearby matrices (the previous decimation
 // iteration's); entries whose FP32 seed does not contract try X_prev before

@@ -37,7 +37,7 @@ rgf_status sliceB(const Ctx& c, int cnt, int ib, const float4* B, const int* act
 static int mm4_planes(const Ctx& c) { return c.m->core == 1 ? kSlices : 4; }
 // C = alpha * A B (+ D) (+ I) from already sliced operands.
 rgf_status mm(const Ctx& c, int cnt, int ia, int ib, float alpha, const float4* D, int addI, float4* C,
-              const int* act) {
+              const int* act, float2* C2) {
     OzGemm g{};
     g.batch = cnt;
     g.m = g.n = g.k = c.b;
@@ -50,6 +50,7 @@ rgf_status mm(const Ctx& c, int cnt, int ia, int ib, float alpha, const float4* 
     g.add_identity = addI;
     g.C = C;
     g.sC = c.nn;
+    g.C2 = C2;
     g.active = act;
     g.status = c.m->status;
     g.bn = c.m->bn;
@@ -310,17 +311,17 @@ rgf_status hp_newton_step(const Ctx& c, int W, double stol, int max_iter, const 
 // with the FP64 Gauss-Jordan inverse.
 // Uses sa[1] for M, sa[0]/sb[0] for the steps and R as df scratch.
 rgf_status inv_mixed(const Ctx& c, int cnt, int W, const float4* M, float4* X, float4* R, const int* act,
-                     int* gj_flags) {
-    return inv_mixed_steps(c, cnt, W, M, X, R, act, gj_flags, 0, c.ns_steps);
+                     int* gj_flags, bool m64_ready) {
+    return inv_mixed_steps(c, cnt, W, M, X, R, act, gj_flags, 0, c.ns_steps, m64_ready);
 }
 
 rgf_status inv_mixed_steps(const Ctx& c, int cnt, int W, const float4* M, float4* X, float4* R, const int* act,
-                           int* gj_flags, int s_begin, int s_end) {
+                           int* gj_flags, int s_begin, int s_end, bool m64_ready) {
     MixedState* m = c.m;
     const int steps = c.ns_steps;
     if (s_end > steps) s_end = steps;
     if (s_begin == 0) {
-        RGF_TRY(dfc_hi_to_c64(cnt, c.b, M, m->c64, act, c.st));
+        if (!m64_ready) RGF_TRY(dfc_hi_to_c64(cnt, c.b, M, m->c64, act, c.st));
         // An FP32 seed with a zero pivot is not reported: its residual is not
         // finite, so it is reseeded in FP64 below, which reports its own pivots.
         RGF_TRY(inv_c32_to(cnt, c.b, m->c64, c.nn, m->inv_ws, nullptr, act, m->status, c.st, m->gj_nb, X, nullptr));
@@ -680,6 +681,9 @@ rgf_status mixed_wave(rgf_plan_s* p, int W) {
 
     // ---------------------------------------------------------- sweep
     float4 *gi = U(4), *P = U(5), *M = U(6), *Q = U(9), *Qn = U(10);
+    // The tcgen05 GEMM that forms M also writes the seed inverse's complex64
+    // input (the legacy mma.sync core does not).
+    float2* m64 = m->core == 0 ? m->c64 : nullptr;
     float4 *G = U(11), *Xt = U(12), *Yt = U(13), *Rs = U(14);
     if (N == 1) {
         FormSrcDf a0{{pm->S_diag, nullptr}, {pm->H_diag, nullptr}, {0, 0}};
@@ -702,7 +706,7 @@ rgf_status mixed_wave(rgf_plan_s* p, int W) {
             RGF_TRY(mm(c, W, 0, 0, -1.0f, nullptr, 0, P, nullptr));  // P = -g tau'
             RGF_TRY(form_slice_rows(W, b, E, eta, Sl, Hl, m->sa[0], m->Kp, st));
             RGF_TRY(sliceB(c, W, 0, P, nullptr));
-            RGF_TRY(mm(c, W, 0, 0, 1.0f, M, 0, M, nullptr));  // M += tau P
+            RGF_TRY(mm(c, W, 0, 0, 1.0f, M, 0, M, nullptr, m64));  // M += tau P (and its complex64 copy)
             if (i == 1) {
                 std::swap(Q, P);
             } else {
@@ -710,7 +714,7 @@ rgf_status mixed_wave(rgf_plan_s* p, int W) {
                 RGF_TRY(mm(c, W, 1, 0, 1.0f, nullptr, 0, Qn, nullptr));  // Q P
                 std::swap(Q, Qn);
             }
-            RGF_TRY(inv_mixed(c, W, W, M, gi, Rs, nullptr, p->d_flags));
+            RGF_TRY(inv_mixed(c, W, W, M, gi, Rs, nullptr, p->d_flags, m64 != nullptr));
         }
         RGF_TRY(sliceA(c, W, 0, Q, nullptr));
         RGF_TRY(sliceB(c, W, 0, gi, nullptr));

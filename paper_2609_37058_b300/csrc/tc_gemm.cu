@@ -226,6 +226,7 @@ struct TcArgs {
     unsigned long long wait_ns;
     int skip_first_chunk;
     int skip0, skip1;  // complex columns left alone (kOutC32)
+    float2* C2;        // kOutDF: C rounded to complex64 as well (optional)
 };
 
 // Output modes: double-float complex (float4), FP64 complex (double2), or
@@ -303,6 +304,7 @@ __device__ __forceinline__ void finish_chunk(const TcArgs& g, const OutT<OM> (&r
             }
             if (g.add_identity && r == c) re = df_add(re, make_float2(1.0f, 0.0f));
             reinterpret_cast<float4*>(g.C)[o] = cdf(re, im);
+            if (g.C2) g.C2[o] = make_float2(re.x + re.y, im.x + im.y);
         }
     }
 }
@@ -1178,7 +1180,7 @@ static int tc_bk() {
 
 rgf_status oz_gemm_tc(const OzGemm& g, cudaStream_t st) {
     TcArgs a{g.batch, g.m, g.n, g.k, g.As, g.Bs, g.Kp, g.alpha, g.D, g.sD, g.add_identity, g.C, g.sC, g.active,
-             g.status, TC_WAIT_NS, 0};
+             g.status, TC_WAIT_NS, 0, 0, 0, g.C2};
     if (g.test_wait_ns) {
         a.wait_ns = g.test_wait_ns;
         a.skip_first_chunk = 1;
