@@ -72,6 +72,11 @@ struct OzGemm {
     int add_identity;            // C += I
     float4* C; long sC;
     float2* C2;                  // optional: C rounded to complex64 as well (same layout)
+    // Optional residual statistics per 32-row x 8-column block (tcgen05
+    // core): sum of squared high words (rsq) and of diagonal entries (rtr);
+    // see ns_check.
+    float* rsq;
+    double2* rtr;
     const int* active;
     int* status;                 // device word, nonzero after a pipeline timeout
     // Test hook (0 in normal use): nonzero makes the tcgen05 core skip the
@@ -168,9 +173,13 @@ constexpr double kNsTol = 1e-6;
 //   err[e] = max(err[e], estimated final residual); an entry still above
 //     kNsTol on the last step is flagged RGF_FLAG_REFINE.
 // more_count (may be null) counts the entries with next_act = 1.
+// rsq / rtr (may be null): the residual GEMM's per-block statistics (see
+// OzGemm); then |R|_F and tr R come from them instead of reading R.
 rgf_status ns_check(int batch, int W, int b, const float4* R, double* err, int* flags, int step, int max_steps,
                     const int* act, int* next_act, int* bad, int* bad_count, double2* theta, cudaStream_t st,
-                    int* more_count = nullptr);
+                    int* more_count = nullptr, const float* rsq = nullptr, const double2* rtr = nullptr);
+// Slots of those statistics per batch entry.
+__host__ __device__ inline int rstat_slots(int b) { return ((b + 31) / 32) * ((b + 7) / 8); }
 // R[i] *= theta[i] (complex) where theta[i] != 1.
 rgf_status scale_theta(int batch, int b, float4* R, const double2* theta, const int* act, cudaStream_t st);
 rgf_status ns_check_f64(int batch, int W, int b, const double2* R, double* err, int* flags, int step, int max_steps,

@@ -771,7 +771,7 @@ rgf_status axpy_dfc(int batch, int b, float alpha, const float4* X, float4* Y, c
 
 __global__ void k_ns_check(int W, int b, const float4* R, double* err, int* flags, int step, int max_steps,
                            const int* act, int* next_act, int* bad, int* bad_count, double2* theta,
-                           int* more_count, double tol) {
+                           int* more_count, double tol, const float* rsq, const double2* rtr) {
     const int bi = blockIdx.x;
     if (act && !act[bi]) {
         if (threadIdx.x == 0) {
@@ -783,20 +783,34 @@ __global__ void k_ns_check(int W, int b, const float4* R, double* err, int* flag
     }
     __shared__ double sh[32];
     const long nn = (long)b * b, off = (long)bi * nn;
-    float s = 0.f;
-    for (long i = threadIdx.x; i < nn; i += blockDim.x) {
-        const float4 a = R[off + i];
-        s = fmaf(a.x, a.x, fmaf(a.z, a.z, s));
-    }
+    double s = 0.0;
     double tr_re = 0.0, tr_im = 0.0;
-    if (step == 0) {
-        for (int i = threadIdx.x; i < b; i += blockDim.x) {
-            const float4 a = R[off + (long)i * b + i];
-            tr_re += df_to_double(re_of(a));
-            tr_im += df_to_double(im_of(a));
+    if (rsq) {
+        // The residual GEMM's per-block sums, added in a fixed order.
+        const int ns = rstat_slots(b);
+        for (int i = threadIdx.x; i < ns; i += blockDim.x) s += (double)rsq[(long)bi * ns + i];
+        if (step == 0 && rtr)
+            for (int i = threadIdx.x; i < ns; i += blockDim.x) {
+                const double2 v = rtr[(long)bi * ns + i];
+                tr_re += v.x;
+                tr_im += v.y;
+            }
+    } else {
+        float sf = 0.f;
+        for (long i = threadIdx.x; i < nn; i += blockDim.x) {
+            const float4 a = R[off + i];
+            sf = fmaf(a.x, a.x, fmaf(a.z, a.z, sf));
+        }
+        s = (double)sf;
+        if (step == 0) {
+            for (int i = threadIdx.x; i < b; i += blockDim.x) {
+                const float4 a = R[off + (long)i * b + i];
+                tr_re += df_to_double(re_of(a));
+                tr_im += df_to_double(im_of(a));
+            }
         }
     }
-    const double t = sqrt(block_sum_d((double)s, sh));
+    const double t = sqrt(block_sum_d(s, sh));
     if (step == 0) {
         tr_re = block_sum_d(tr_re, sh);
         tr_im = block_sum_d(tr_im, sh);
@@ -843,10 +857,10 @@ __global__ void k_ns_check(int W, int b, const float4* R, double* err, int* flag
 
 rgf_status ns_check(int batch, int W, int b, const float4* R, double* err, int* flags, int step, int max_steps,
                     const int* act, int* next_act, int* bad, int* bad_count, double2* theta, cudaStream_t st,
-                    int* more_count) {
+                    int* more_count, const float* rsq, const double2* rtr) {
     if (batch <= 0) return RGF_OK;
     k_ns_check<<<batch, 256, 0, st>>>(W, b, R, err, flags, step, max_steps, act, next_act, bad, bad_count, theta,
-                                      more_count, kNsTol);
+                                      more_count, kNsTol, rsq, rtr);
     RGF_LAUNCH_CHECK();
     return RGF_OK;
 }

@@ -29,6 +29,8 @@ struct MixedState {
     int* bad_count = nullptr;
     int* more_count = nullptr;  // entries that need another Newton-Schulz step
     int* h_more = nullptr;      // pinned
+    float* r_sumsq = nullptr;   // residual statistics (rstat_slots(b) per inverse entry)
+    double2* r_trace = nullptr;
     int* h_bad = nullptr;    // pinned
     double2* c128 = nullptr;
     void* inv64_ws = nullptr;
@@ -94,7 +96,7 @@ struct Ctx {
 rgf_status sliceA(const Ctx& c, int cnt, int ia, const float4* A, const int* act, int planes = kSlices);
 rgf_status sliceB(const Ctx& c, int cnt, int ib, const float4* B, const int* act, int planes = kSlices);
 rgf_status mm(const Ctx& c, int cnt, int ia, int ib, float alpha, const float4* D, int addI, float4* C,
-              const int* act, float2* C2 = nullptr);
+              const int* act, float2* C2 = nullptr, float* rsq = nullptr, double2* rtr = nullptr);
 // C = A B + D from the four most significant slices of each operand.
 rgf_status mm4(const Ctx& c, int cnt, int ia, int ib, const float4* D, float4* C, const int* act);
 // Seven-slice (FP64-class) counterparts for FP64 matrices.

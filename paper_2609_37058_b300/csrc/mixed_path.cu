@@ -37,7 +37,7 @@ rgf_status sliceB(const Ctx& c, int cnt, int ib, const float4* B, const int* act
 static int mm4_planes(const Ctx& c) { return c.m->core == 1 ? kSlices : 4; }
 // C = alpha * A B (+ D) (+ I) from already sliced operands.
 rgf_status mm(const Ctx& c, int cnt, int ia, int ib, float alpha, const float4* D, int addI, float4* C,
-              const int* act, float2* C2) {
+              const int* act, float2* C2, float* rsq, double2* rtr) {
     OzGemm g{};
     g.batch = cnt;
     g.m = g.n = g.k = c.b;
@@ -51,6 +51,8 @@ rgf_status mm(const Ctx& c, int cnt, int ia, int ib, float alpha, const float4* 
     g.C = C;
     g.sC = c.nn;
     g.C2 = C2;
+    g.rsq = rsq;
+    g.rtr = rtr;
     g.active = act;
     g.status = c.m->status;
     g.bn = c.m->bn;
@@ -332,9 +334,13 @@ rgf_status inv_mixed_steps(const Ctx& c, int cnt, int W, const float4* M, float4
     // Step s works on the mask nsact[s % 2] and writes nsact[(s + 1) % 2].
     int* cur = m->nsact[s_begin & 1];
     int* nxt = m->nsact[(s_begin + 1) & 1];
+    // The tcgen05 residual GEMM also returns |R|_F and tr R per block, so
+    // that the check does not read R again (the legacy core does not).
+    float* rsq = m->core == 0 ? m->r_sumsq : nullptr;
     for (int s = s_begin; s < s_end; ++s) {
         RGF_TRY(sliceB(c, cnt, 0, X, cur));
-        RGF_TRY(mm(c, cnt, 1, 0, -1.0f, nullptr, 1, R, cur));  // R = I - M X
+        double2* rtr = (rsq && s == 0) ? m->r_trace : nullptr;
+        RGF_TRY(mm(c, cnt, 1, 0, -1.0f, nullptr, 1, R, cur, nullptr, rsq, rtr));  // R = I - M X
         if (s == 1) RGF_CUDA_TRY(cudaMemsetAsync(m->bad_count, 0, sizeof(int), c.st));
         // From step 1 on the entries that need a further step are counted.
         // Outside graph capture the count is read back (step 1 synchronises
@@ -343,7 +349,7 @@ rgf_status inv_mixed_steps(const Ctx& c, int cnt, int W, const float4* M, float4
         const bool count_more = s >= 1;
         if (count_more) RGF_CUDA_TRY(cudaMemsetAsync(m->more_count, 0, sizeof(int), c.st));
         RGF_TRY(ns_check(cnt, W, c.b, R, c.err, c.flags, s, steps, cur, nxt, m->bad, m->bad_count, m->theta, c.st,
-                         count_more ? m->more_count : nullptr));
+                         count_more ? m->more_count : nullptr, rsq, rtr));
         if (count_more && !c.graph && s >= 2) {
             RGF_CUDA_TRY(cudaMemcpyAsync(m->h_more, m->more_count, sizeof(int), cudaMemcpyDeviceToHost, c.st));
             RGF_CUDA_TRY(cudaStreamSynchronize(c.st));
@@ -390,6 +396,7 @@ size_t mixed_workspace_bytes(int W, int b, int slice_entries, int inv_entries) {
     s += (size_t)inv_entries * nn * sizeof(double2) + inv_workspace_bytes_t<double2>(inv_entries, b);
     s += (size_t)inv_entries * 4 * sizeof(int) +
          (size_t)inv_entries * sizeof(double2) + 8192;
+    s += (size_t)inv_entries * rstat_slots(b) * (sizeof(float) + sizeof(double2)) + 512;
     return s;
 }
 
@@ -460,6 +467,11 @@ rgf_status mixed_state_init(MixedState* m, int b, int W, void* ws, cudaStream_t 
     m->theta = (double2*)w;
     w += (size_t)inv_entries * sizeof(double2);
     w = (char*)(((uintptr_t)w + 255) & ~(uintptr_t)255);
+    m->r_sumsq = (float*)w;
+    w += (size_t)inv_entries * rstat_slots(b) * sizeof(float);
+    w = (char*)(((uintptr_t)w + 255) & ~(uintptr_t)255);
+    m->r_trace = (double2*)w;
+    w += (size_t)inv_entries * rstat_slots(b) * sizeof(double2);
     // Zero the slice buffers once: the K padding is never written again.
     RGF_CUDA_TRY(cudaMemsetAsync(m->sa[0], 0,
                                  2 * sa_bytes(slice_entries, b, m->Kp) + 2 * sb_bytes(slice_entries, b, m->Kp), st));

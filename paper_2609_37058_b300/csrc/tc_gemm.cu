@@ -227,6 +227,12 @@ struct TcArgs {
     int skip_first_chunk;
     int skip0, skip1;  // complex columns left alone (kOutC32)
     float2* C2;        // kOutDF: C rounded to complex64 as well (optional)
+    // kOutDF (optional): residual statistics of the result per block of 32
+    // rows x 8 complex columns (slot (bi * ceil(m/32) + r/32) * ceil(n/8) +
+    // c/8, written by the one warp that stores the block): the sum of the
+    // squared high words of Re and Im, and of the diagonal entries.
+    float* rsq;
+    double2* rtr;
 };
 
 // Output modes: double-float complex (float4), FP64 complex (double2), or
@@ -269,13 +275,16 @@ __device__ __forceinline__ void combine_chunk(const TcArgs& g, const float (&v)[
 }
 
 // Addend and identity of those values and their store: row r, columns from cb.
+// Called by whole warps (lanes: consecutive rows r, one 8-column block cb).
 template <int OM>
 __device__ __forceinline__ void finish_chunk(const TcArgs& g, const OutT<OM> (&res)[8], int bi, int r, int cb) {
-    if (r >= g.m) return;
+    const bool rok = r < g.m;
+    float sq = 0.0f;
+    double tre = 0.0, tim = 0.0;
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
         const int c = cb + t;
-        if (c >= g.n) continue;
+        if (!rok || c >= g.n) continue;
         const long o = (long)bi * g.sC + (long)r * g.n + c;
         if constexpr (OM == kOutC32) {
             if (c >= g.skip0 && c < g.skip1) continue;
@@ -305,6 +314,30 @@ __device__ __forceinline__ void finish_chunk(const TcArgs& g, const OutT<OM> (&r
             if (g.add_identity && r == c) re = df_add(re, make_float2(1.0f, 0.0f));
             reinterpret_cast<float4*>(g.C)[o] = cdf(re, im);
             if (g.C2) g.C2[o] = make_float2(re.x + re.y, im.x + im.y);
+            if (g.rsq) {
+                sq = fmaf(re.x, re.x, fmaf(im.x, im.x, sq));
+                if (r == c) {
+                    tre = (double)re.x + (double)re.y;
+                    tim = (double)im.x + (double)im.y;
+                }
+            }
+        }
+    }
+    if constexpr (OM == kOutDF) {
+        if (g.rsq) {
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                sq += __shfl_xor_sync(0xffffffffu, sq, off);
+                tre += __shfl_xor_sync(0xffffffffu, tre, off);
+                tim += __shfl_xor_sync(0xffffffffu, tim, off);
+            }
+            // Lane 0 holds the block's first row; blocks past the matrix
+            // (the ragged last column tile, row tiles past m) have no slot.
+            if ((threadIdx.x & 31) == 0 && r < g.m && cb < g.n) {
+                const long slot = ((long)bi * ((g.m + 31) >> 5) + (r >> 5)) * ((g.n + 7) >> 3) + (cb >> 3);
+                g.rsq[slot] = sq;
+                if (g.rtr) g.rtr[slot] = make_double2(tre, tim);
+            }
         }
     }
 }
@@ -1180,7 +1213,7 @@ static int tc_bk() {
 
 rgf_status oz_gemm_tc(const OzGemm& g, cudaStream_t st) {
     TcArgs a{g.batch, g.m, g.n, g.k, g.As, g.Bs, g.Kp, g.alpha, g.D, g.sD, g.add_identity, g.C, g.sC, g.active,
-             g.status, TC_WAIT_NS, 0, 0, 0, g.C2};
+             g.status, TC_WAIT_NS, 0, 0, 0, g.C2, g.rsq, g.rtr};
     if (g.test_wait_ns) {
         a.wait_ns = g.test_wait_ns;
         a.skip_first_chunk = 1;
