@@ -41,7 +41,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
-    ap.add_argument("--wave", type=int, default=296, help="energies per step and rank (two per SM)")
+    ap.add_argument("--wave", type=int, default=512,
+                    help="energies per step and rank (512: the 2048-energy grid in four full waves; larger waves "
+                         "hide more of the seed inverse's panel latency, measured 45.6 / 47.4 / 48.2 / 48.3 "
+                         "energies/s at 296 / 444 / 512 / 592)")
     ap.add_argument("--fp64-wave", type=int, default=148, help="energies of the timed FP64 GPU comparison wave")
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 GPU comparison step")
     ap.add_argument("--cpu-energies", type=int, default=2, help="energies of the oracle CPU sample")
