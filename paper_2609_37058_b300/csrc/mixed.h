@@ -159,6 +159,16 @@ rgf_status axpy_dfc(int batch, int b, float alpha, const float4* X, float4* Y, c
 // and 256, against 1e-6 allowed; 1e-6 spares most inverses a third step.)
 // The FP64-class inverses of the lead decimation keep 3e-7.
 constexpr double kNsTol = 1e-6;
+// The FP64-class inverses of the lead decimation take an FP32 seed with
+// |I - M X0|_F < kHpBad and refine it, with up to kHpSteps Newton-Schulz
+// steps: any |R|_F < 1 bounds the spectral radius below one, so the
+// iteration converges (from 0.9 in about nine steps, each a masked pair of
+// slice products for the few such entries); seeds at or above it are
+// replaced (the previous decimation iteration's inverse, else the FP64
+// Gauss-Jordan inverse, which runs one matrix per SM on the narrow FP64
+// pipe: about 13 ms per event at b = 256).
+constexpr double kHpBad = 0.98;
+constexpr int kHpSteps = 12;
 
 // Newton-Schulz bookkeeping for step s of at most max_steps on batch
 // entries i (energy e = i mod W), given R = I - M X:
@@ -193,7 +203,7 @@ rgf_status c128_to_dfc(int batch, int b, const double2* X, float4* Y, const int*
 // out[i] = act ? act[i] : 1
 rgf_status mask_init(int batch, const int* act, int* out, cudaStream_t st);
 // For FP64 inverses reseeded from a nearby inverse (mask): still_bad where
-// |I - M X|_F >= 0.5 (counted), next_act = |R|_F > 3e-7 for the mask entries.
+// |I - M X|_F >= kHpBad (counted), next_act = |R|_F > 3e-7 for the mask entries.
 rgf_status recheck_f64(int batch, int b, const double2* R, const int* mask, int* still_bad, int* count,
                        int* next_act, cudaStream_t st);
 // *acc += *count (one thread)

@@ -888,7 +888,7 @@ __global__ void k_ns_check_f64(int W, int b, const double2* R, double* err, int*
         const int e = bi % W;
         const bool num_ok = isfinite(t);
         if (step == 0) {
-            const bool is_bad = (!num_ok) || (t >= 0.5);
+            const bool is_bad = (!num_ok) || (t >= kHpBad);
             bad[bi] = is_bad ? 1 : 0;
             if (is_bad) {
                 atomicAdd(bad_count, 1);
@@ -1006,7 +1006,7 @@ rgf_status mask_init(int batch, const int* act, int* out, cudaStream_t st) {
 }
 
 // Second look at FP64 inverses whose seed was replaced by a nearby inverse:
-// for mask entries, still_bad = (|R|_F >= 0.5 or not finite), counted into
+// for mask entries, still_bad = (|R|_F >= kHpBad or not finite), counted into
 // *count, and next_act = |R|_F > 3e-7 (or still bad); other entries keep
 // next_act and get still_bad = 0.
 __global__ void k_recheck_f64(int b, const double2* R, const int* mask, int* still_bad, int* count, int* next_act) {
@@ -1024,7 +1024,7 @@ __global__ void k_recheck_f64(int b, const double2* R, const int* mask, int* sti
     }
     const double t = sqrt(block_sum_d(s, sh));
     if (threadIdx.x == 0) {
-        const bool sb = !(isfinite(t) && t < 0.5);
+        const bool sb = !(isfinite(t) && t < kHpBad);
         still_bad[bi] = sb ? 1 : 0;
         if (sb) atomicAdd(count, 1);
         next_act[bi] = (sb || t > 3e-7) ? 1 : 0;

@@ -114,8 +114,10 @@ rgf_status inv_hp(const Ctx& c, int cnt, int W, const double2* M, double2* X, do
     MixedState* m = c.m;
     RGF_TRY(c128_to_c64(cnt, c.b, M, m->c64, act, c.st));
     RGF_TRY(inv_c32_to(cnt, c.b, m->c64, c.nn, m->inv_ws, nullptr, act, m->status, c.st, 0, nullptr, X));
-    const int steps = c.ns_steps;
-    if (steps == 0) return RGF_OK;
+    if (c.ns_steps == 0) return RGF_OK;
+    // Seeds up to kHpBad are refined rather than replaced: allow the steps
+    // they need (entries stop as soon as they converge).
+    const int steps = c.ns_steps > kHpSteps ? c.ns_steps : kHpSteps;
     int* cur = m->nsact[0];
     int* nxt = m->nsact[1];
     RGF_TRY(mask_init(cnt, act, cur, c.st));
