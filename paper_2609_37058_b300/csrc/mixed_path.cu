@@ -174,6 +174,13 @@ rgf_status inv_hp(const Ctx& c, int cnt, int W, const double2* M, double2* X, do
 // of the decimation pool, with FP64 storage and seven-slice products, then
 // one Newton step on the fixed-point equation for the converged entries
 // (see hp_newton_step).
+// The doubling's remainder after round k is A^(2^k) X B^(2^k), at most
+// |A^(2^k)|_F |B^(2^k)|_F |X|_F: stopping at a product of 1e-4 leaves X
+// accurate to 1e-4 relative.  X is a correction (a second step, taken while
+// |X|_F > 1e-8 |g|_F, solves again from the corrected g), so g keeps at most
+// 1e-12 relative from the truncation.
+constexpr double kSteinTol = 1e-4;
+
 rgf_status hp_newton_step(const Ctx& c, int W, double stol, int max_iter, const double2* a0, const double2* al0,
                           const double2* be0, double2* g);
 
@@ -226,7 +233,7 @@ rgf_status hp_decimate_run(const Ctx& c, int W, double tol, int max_iter, double
     RGF_TRY(merge_dec_flags(W, m->dec_flags, m->dec_active, c.flags, st));
     RGF_TRY(inv_hp(c, W2, W, eps_s, g, R, nullptr, m->dec_flags));
     RGF_TRY(merge_dec_flags(W, m->dec_flags, m->dec_active, c.flags, st));
-    RGF_TRY(hp_newton_step(c, W, tol * tol, max_iter, U(26), U(28), U(30), g));
+    RGF_TRY(hp_newton_step(c, W, kSteinTol, max_iter, U(26), U(28), U(30), g));
     RGF_TRY(merge_dec_flags(W, m->dec_flags, m->dec_active, c.flags, st));
     *g_out = g;
     return RGF_OK;
