@@ -1277,12 +1277,23 @@ rgf_status gj_update_tc(int batch, int b, int nbk, const __nv_bfloat16* Ps, cons
 rgf_status oz_gemm_hp(const OzGemmHP& g, cudaStream_t st) {
     TcArgs a{g.batch, g.m, g.n, g.k, g.As, g.Bs, g.Kp, g.alpha, g.D, g.sD, g.add_identity, g.C, g.sC, g.active,
              g.status, TC_WAIT_NS, 0};
-    if (g.nsl == 5) return launch_tc<5, 5, 80, kOutF64, 32, kSlicesHP>(a, st);
+    // Tiles 64 wide: 2n = 512 real columns in eight whole tiles (80 wide
+    // needs seven, the last 32 wide, and measured 3% slower in the lead
+    // decimation); RGF_HP_BN=80 in the environment (read once) selects 80.
+    static const bool bn64 = [] {
+        const char* e = getenv("RGF_HP_BN");
+        return !(e && e[0] == '8' && e[1] == '0');
+    }();
+    if (g.nsl == 5) {
+        if (bn64) return launch_tc<5, 5, 64, kOutF64, 32, kSlicesHP>(a, st);
+        return launch_tc<5, 5, 80, kOutF64, 32, kSlicesHP>(a, st);
+    }
     if (g.nsl != 0 && g.nsl != kSlicesHP) {
         set_error("oz_gemm_hp: unsupported slice count %d", g.nsl);
         return RGF_E_INVALID;
     }
     if (tc_bk() == 16) return launch_tc<kSlicesHP, kGroupsHP, 80, kOutF64, 16>(a, st);
+    if (bn64) return launch_tc<kSlicesHP, kGroupsHP, 64, kOutF64, 32>(a, st);
     return launch_tc<kSlicesHP, kGroupsHP, 80, kOutF64, 32>(a, st);
 }
 
