@@ -456,6 +456,7 @@ rgf_status mixed_state_init(MixedState* m, int b, int W, void* ws, cudaStream_t 
     }
     m->c64 = (float2*)w;
     w += (size_t)inv_entries * nn * sizeof(float2);
+    w = (char*)(((uintptr_t)w + 255) & ~(uintptr_t)255);  // the seed's BF16 splits are read by TMA
     m->inv_ws = (void*)w;
     w += inv_c32_workspace_bytes(inv_entries, b);
     w = (char*)(((uintptr_t)w + 255) & ~(uintptr_t)255);
