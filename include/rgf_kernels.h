@@ -25,7 +25,11 @@ rgf_status rgf_kernel_zgemm_f64(int batch, int m, int n, int k, const double* A,
 rgf_status rgf_kernel_inverse_f64(int batch, int b, double* A, int* flags);
 
 /* In-place FP32 inverse (the mixed path's seed): A holds complex64 values
- * as (re, im) float pairs. */
+ * as (re, im) float pairs.  Blocked Gauss-Jordan with partial pivoting: the
+ * 32-column panels on the CUDA cores, each trailing update on the tensor
+ * cores (three BF16 splits per operand, FP32 accumulation, FP32-accurate;
+ * RGF_GJ_TC=0 in the environment selects CUDA-core updates).  Returns
+ * RGF_E_CUDA if the tensor-core pipeline's bounded waits run out. */
 rgf_status rgf_kernel_inverse_c64(int batch, int b, float* A, int* flags);
 
 /* C[i] = A[i] B[i] by the mixed path's slice-product GEMM: A and B are
