@@ -339,7 +339,7 @@ __global__ void __launch_bounds__(256) k_gj_panel(int b, int k0, int nbk, T2* A,
             // Branch-free over lanes: lane jj takes -f / pivot, the others
             // x - f p_j.
             const T2 mid = C::make(-inv_d.x, -inv_d.y);
-#pragma unroll 4
+#pragma unroll 8
             for (int r = wid; r < b; r += NW) {
                 const T2 f = fcol[r];
                 const T2 x = pan[r * P + lane];
